@@ -1,0 +1,343 @@
+#!/usr/bin/env python
+"""Throughput of the fused 25-point acoustic wave step (grid-point updates/s).
+
+A "step" is one leapfrog time step of the whole hot path (Laplacian, update,
+taper, source, receivers) over the 1024^3 layered survey: FP32 fields,
+h = 10 m, dt at CFL 0.4, 20-cell absorbing layer on every face, one 10 Hz
+Ricker at (512, 512, 20), 32 x 32 receivers on k = 20. Inputs (three 4.4 GB
+fields per step) are far larger than L2, so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line on rank 0. Under torchrun each rank advances its own
+replica of the survey (the problem does not need an exchange between GPUs
+to be benchmarked; replicas only), and the time is the maximum over ranks.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gpoint-updates/s & % of HBM roofline, 25-pt wave step, FP32 vs BF16 at stated err"
+UNIT = "Gpoint-updates/s"
+BYTES_PER_POINT = 16  # read u^n, u^{n-1}, (V dt/h)^2; write u^{n+1} (FP32)
+FALLBACK_HBM_GBS = 6800.0
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "step_stream_layered1024_ncu.txt")
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_2204_03775_gb300", "csrc", f)
+                  for f in ("ws_kernels_stream.cu", "ws_internal.h")]
+
+
+def parse_args():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawTextHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--size", type=int, default=1024, help="cells per axis (default 1024)")
+    ap.add_argument("--kernel", choices=["auto", "stream", "direct"], default="auto")
+    ap.add_argument("--tile", default="0x0", help="streaming tile, e.g. 64x16 (0x0 = default)")
+    ap.add_argument("--zblock", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def kernel_sources_digest() -> str:
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        with open(p, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def recorded_traffic():
+    """DRAM bytes per launch from the committed ncu summary, if it matches the kernel source."""
+    try:
+        fields = {}
+        with open(TRAFFIC_FILE) as f:
+            for line in f:
+                if ":" in line:
+                    k, v = line.split(":", 1)
+                    fields[k.strip()] = v.strip()
+        if fields.get("kernel_sources_sha256") != kernel_sources_digest():
+            return None
+        if fields.get("workload_cells") != str(1024 ** 3):
+            return None
+        return float(fields["traffic_bytes_per_launch"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+def measured_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons while it runs."""
+
+    FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw",
+              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, gpu_id):
+        self.proc = None
+        self.gpu_id = gpu_id
+
+    def __enter__(self):
+        cmd = ["nvidia-smi", f"--query-gpu={','.join(self.FIELDS)}",
+               "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.gpu_id:
+            cmd += ["-i", self.gpu_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                         text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        if self.proc is None:
+            return None
+        rows = []
+        for line in (self.out or "").splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) != len(self.FIELDS):
+                continue
+            try:
+                rows.append((float(parts[0]), float(parts[1]), parts[3:]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, flags in rows for i, f in enumerate(flags)
+                          if f.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows),
+                "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup(n_gpus):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world != n_gpus and world > 1:
+        raise SystemExit(f"--gpus {n_gpus} but WORLD_SIZE={world}")
+    return world, rank, local
+
+
+def cpu_baseline(w, target_s=15.0):
+    """The FP64 oracle on a bounded slab of the same survey (host cores)."""
+    import numpy as np
+    import oracle
+
+    oracle.build()
+    # calibrate on two steps of a 4-plane slab, then size the sample to ~target_s
+    t0 = time.perf_counter()
+    oracle.run(w.vel[:4], w.h, w.dt, 2, sponge=w.sponge, window=(0, 0, 0, w.nx, w.ny, w.nz))
+    rate = 2 * 4 * w.nx * w.ny / (time.perf_counter() - t0)
+    depth = int(min(w.nz, max(w.sources[0][2] + 5, 32)))
+    steps = int(max(2, min(40, target_s * rate / (depth * w.nx * w.ny))))
+    slab = np.ascontiguousarray(w.vel[:depth])
+    t0 = time.perf_counter()
+    oracle.run(slab, w.h, w.dt, steps, sources=w.sources, receivers=None, sponge=w.sponge,
+               window=(0, 0, 0, w.nx, w.ny, w.nz))
+    el = time.perf_counter() - t0
+    pts = depth * w.nx * w.ny * steps
+    return {"value": pts / el / 1e9, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"FP64 oracle, top slab k in [0,{depth}) of the {w.nx}x{w.ny}x{w.nz} "
+                      f"survey (same model, taper, source), {steps} steps from rest, "
+                      f"{el:.1f} s wall"}
+
+
+def run_reference(args):
+    """The oracle as it stands, timed on the host cores (rank 0 only)."""
+    world, rank, _ = dist_setup(args.gpus)
+    if rank != 0:
+        return
+    import numpy as np
+    import oracle
+    from paper_2204_03775_gb300 import synthetic
+
+    oracle.build()
+    n = args.size
+    w = synthetic.layered_survey(n, n, n, nt=args.steps + args.warmup)
+    # per-step sample: a top slab sized so that warm-up + timed steps take ~2 minutes
+    t0 = time.perf_counter()
+    oracle.run(w.vel[:4], w.h, w.dt, 2, sponge=w.sponge, window=(0, 0, 0, n, n, n))
+    rate = 2 * 4 * n * n / (time.perf_counter() - t0)
+    depth = int(max(1, min(64, 120.0 * rate / ((args.steps + args.warmup) * n * n))))
+    src = [s for s in w.sources if s[2] < depth]
+    slab = np.ascontiguousarray(w.vel[:depth])
+    win = (0, 0, 0, n, n, n)
+    warm = oracle.run(slab, w.h, w.dt, args.warmup, sources=src, sponge=w.sponge, window=win)
+    t0 = time.perf_counter()
+    oracle.run(slab, w.h, w.dt, args.steps, sources=src, sponge=w.sponge, window=win,
+               u_init=warm["u"], uprev_init=warm["u_prev"], n0=args.warmup)
+    el = time.perf_counter() - t0
+    pts = depth * n * n * args.steps
+    value = pts / el / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"layered_survey {n}x{n}x{n}", "sample_depth": depth,
+                   "parallelism": "host cores (OpenMP)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(),
+                         "kind": "oracle",
+                         "sample": f"top slab k in [0,{depth}) of the survey per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    import paper_2204_03775_gb300 as wsb
+    from paper_2204_03775_gb300 import synthetic
+
+    world, rank, local = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    wsb.load_library(build_if_missing=True)
+
+    n = args.size
+    K, W = args.steps, args.warmup
+    w = synthetic.layered_survey(n, n, n, nt=K + W)
+    npts = w.points
+    stream = torch.cuda.current_stream()
+
+    h = wsb.ws_create(w.nx, w.ny, w.nz, w.h, w.dt)
+    wsb.ws_set_stream(h, stream)
+    kern = {"auto": wsb.WS_KERNEL_AUTO, "stream": wsb.WS_KERNEL_STREAM,
+            "direct": wsb.WS_KERNEL_DIRECT}[args.kernel]
+    tx, ty = (int(x) for x in args.tile.split("x"))
+    wsb.ws_set_kernel(h, kern, tx, ty, args.zblock)
+    wsb.ws_set_velocity(h, w.vel)
+    wsb.ws_set_sponge(h, *w.sponge)
+    for s in w.sources:
+        wsb.ws_add_source(h, *s)
+    wsb.ws_set_receivers(h, w.receivers, K + W)
+
+    wsb.ws_step(h, W)
+    wsb.ws_synchronize(h)
+
+    props = torch.cuda.get_device_properties(local)
+    gpu_id = f"GPU-{props.uuid}" if getattr(props, "uuid", None) else None
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(K + 1)]
+    launches0 = wsb.ws_launch_count(h)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(gpu_id) as clk:
+        evs[0].record(stream)
+        for s in range(K):
+            wsb.ws_step(h, 1)
+            evs[s + 1].record(stream)
+        torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    wsb.ws_synchronize(h)
+    launches = wsb.ws_launch_count(h) - launches0
+    elapsed = evs[0].elapsed_time(evs[K]) / 1e3
+    per_launch = [evs[s].elapsed_time(evs[s + 1]) / 1e3 for s in range(K)]
+    if dist is not None:
+        t = torch.tensor([elapsed], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+
+    # end to end through the public API from pinned host memory: upload the
+    # model, run the K steps, read the traces back
+    e2e = None
+    if not args.no_e2e:
+        vel_pinned = torch.from_numpy(w.vel).pin_memory()
+        wsb.ws_write_field(h, None, None, 0)
+        wsb.ws_set_receivers(h, w.receivers, K)
+        traces = torch.empty((len(w.receivers), K), dtype=torch.float32).pin_memory()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        wsb.ws_set_velocity(h, vel_pinned)
+        wsb.ws_step(h, K)
+        wsb.ws_read_traces(h, traces)
+        e2e_s = time.perf_counter() - t0
+        if dist is not None:
+            t = torch.tensor([e2e_s], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        e2e = {"value": world * npts * K / e2e_s / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": vel_pinned.numel() * 4 / K,
+               "d2h_bytes_per_step": traces.numel() * 4 / K,
+               "what": "ws_set_velocity (pinned host model) + ws_step(K) + ws_read_traces (pinned host)"}
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    avg_launch = statistics.mean(per_launch)
+    peak, peak_kind = measured_peak()
+    achieved = BYTES_PER_POINT * npts / avg_launch / 1e9
+    value = world * npts * K / elapsed / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": 1e3 * elapsed / K, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"layered_survey {n}x{n}x{n}, h=10 m, CFL 0.4, 20-cell Cerjan "
+                               f"layer, 10 Hz Ricker at ({n // 2},{n // 2},20), 32x32 receivers "
+                               f"at k=20", "kernel": args.kernel, "tile": args.tile,
+                   "zblock": args.zblock, "l2": "inputs larger than L2 (3 x 4.4 GB per step)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": recorded_traffic(),
+                     "peak_source": peak_kind,
+                     "bytes_per_point": BYTES_PER_POINT,
+                     "kernel_ms": 1e3 * avg_launch},
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+        "e2e": e2e,
+    }
+    wsb.ws_destroy(h)
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w)
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,153 @@
+/*
+ * wavestep.h -- C ABI of the GB300 (sm_103a) stepper for the 3D
+ * constant-density acoustic wave equation of arXiv 2204.03775.
+ *
+ * The library advances Eq. 2 of the paper (Section II),
+ *
+ *     u^{n+1} - Q u^n + u^{n-1} = dt^2 V^2 f^n,   Q = 2 + dt^2 V^2 Lap,
+ *
+ * with Lap the 25-point, 8th-order star Laplacian of Section II (four
+ * neighbours per side on each axis; weights c_0..c_4 = -205/72, 8/5, -1/5,
+ * 8/315, -1/560 divided by h^2, the centre weight applied once per axis as in
+ * Section III-C-2), in the time loop of Algorithm 1 starting from
+ * u^{-1} = u^0 = 0. Each step is one fused pass on the GPU that also applies
+ * an absorbing taper, injects Ricker sources and records receivers; the paper
+ * leaves boundary conditions and I/O unevaluated (Section II), so those three
+ * are this library's additions, defined below.
+ *
+ * Conventions for every entry point:
+ *  - Return value: WS_OK (0) on success, a negative WS_ERR_* code otherwise;
+ *    ws_last_error() then returns a message (per calling thread).
+ *  - Grid: interior cells (i, j, k), 0 <= i < nx, 0 <= j < ny, 0 <= k < nz,
+ *    spacing h (metres) on all axes, k = 0 the top plane. Outside the interior
+ *    the field is zero at all times (a 4-cell zero-Dirichlet halo).
+ *  - User arrays of the grid are unpadded, [nz][ny][nx] row-major, x fastest,
+ *    float32. The library keeps its own padded copies in device memory; it
+ *    never keeps a pointer it was given.
+ *  - on_device: 0 = the pointer is host memory (any, pinned is faster),
+ *    1 = device memory of the current CUDA device.
+ *  - Work is issued on the handle's stream (ws_set_stream; default: the
+ *    legacy default stream). Calls that read into host memory synchronize
+ *    that stream before returning; the others are asynchronous.
+ *  - A handle is not thread-safe; distinct handles are independent.
+ *  - Device memory: the handle allocates (cudaMalloc) three padded fields of
+ *    (nx+8 rounded up to 4) * (ny+8) * (nz+8) floats plus O(nx+ny+nz) and the
+ *    trace buffer; ws_destroy frees them.
+ */
+#ifndef WAVESTEP_H
+#define WAVESTEP_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define WS_OK            0
+#define WS_ERR_BADARG   -1  /* invalid argument or size */
+#define WS_ERR_CFL      -2  /* velocity model violates the stability limit */
+#define WS_ERR_OOM      -3  /* device allocation failed */
+#define WS_ERR_CUDA     -4  /* CUDA runtime or driver error */
+#define WS_ERR_TIMEOUT  -5  /* a bounded device-side wait ran out */
+#define WS_ERR_STATE    -6  /* call not valid in the handle's current state */
+
+/* Step kernels selectable with ws_set_kernel. */
+#define WS_KERNEL_AUTO    0  /* the streaming kernel when the grid fits its tile, else DIRECT */
+#define WS_KERNEL_DIRECT  1  /* one thread per cell, neighbours loaded from global memory */
+#define WS_KERNEL_STREAM  2  /* z-streaming: TMA-staged xy tiles + 9-plane register queue */
+
+#define WS_MAX_SOURCES   16
+
+typedef struct ws_handle *ws_t;
+
+/* Create a stepper for an nx x ny x nz grid with spacing h (m) and time step
+ * dt (s). Fields start at zero, the step counter at 0, damping off, no
+ * sources or receivers, and no velocity (ws_step fails until
+ * ws_set_velocity succeeds). Sizes must be >= 1 and each <= 65535.
+ * Errors: BADARG, OOM, CUDA. On error *out is NULL. */
+int ws_create(ws_t *out, int nx, int ny, int nz, double h, double dt);
+
+/* Free every device and host resource of the handle (synchronizes its
+ * stream first). NULL is accepted. */
+int ws_destroy(ws_t ws);
+
+/* Issue all further work on cuda_stream (a cudaStream_t of the current
+ * device; NULL = legacy default stream). The caller keeps the stream alive
+ * for as long as the handle uses it. */
+int ws_set_stream(ws_t ws, void *cuda_stream);
+
+/* Set the velocity model V of Eq. 1 (m/s), [nz][ny][nx]. The library stores
+ * (V dt / h)^2 in its padded layout (computed in double, rounded to float).
+ * Every value must be finite and > 0, and max(V) dt / h must not exceed the
+ * leapfrog stability limit of this Laplacian, 2 / sqrt(3 * sum_m |w_m|) with
+ * w the 1D weights (about 0.4529); else CFL (the previous model, if any, is
+ * then no longer valid and ws_step fails until a valid one is set).
+ * Synchronizes the stream (it reads back the model's extrema). */
+int ws_set_velocity(ws_t ws, const float *v, int on_device);
+
+/* Absorbing taper (Cerjan et al. 1985): for a cell at distance d < nb cells
+ * from the nearer outer face of an axis, that axis contributes
+ * exp(-(a (nb - d))^2); g = gx(i) gy(j) gz(k) and each step computes
+ *     u^{n+1} = g (2 u^n - g u^{n-1} + (V dt)^2 Lap u^n),
+ * i.e. both time levels are multiplied by g after each plain step of Eq. 2.
+ * nb = 0 turns damping off. Requires 0 <= nb and 0 <= a. */
+int ws_set_sponge(ws_t ws, int nb, double a);
+
+/* Add a point source at cell (ix, iy, iz) with Ricker time function
+ *     s(t) = amp (1 - 2 pi^2 f0^2 (t - t0)^2) exp(-pi^2 f0^2 (t - t0)^2).
+ * Step n (producing u^{n+1}, t_n = n dt) adds (V_s dt)^2 s(t_n) at the cell
+ * after damping: the right-hand side dt^2 V^2 f^n of Eq. 2. Up to
+ * WS_MAX_SOURCES sources. Errors: BADARG (cell outside the grid, f0 <= 0,
+ * too many sources). */
+int ws_add_source(ws_t ws, int ix, int iy, int iz, double f0, double t0, double amp);
+
+/* Remove every source. */
+int ws_clear_sources(ws_t ws);
+
+/* Record u^{n+1} at nrec cells after each step n, for steps 0..nt_max-1
+ * counted from the step at which this call is made (the trace clock
+ * restarts here; traces are zeroed). ijk is host memory, [nrec][3] =
+ * (i, j, k) per receiver, copied. nrec = 0 removes all receivers. Stepping
+ * past nt_max recorded steps fails with STATE. */
+int ws_set_receivers(ws_t ws, int nrec, const int *ijk, int nt_max);
+
+/* Advance nsteps steps (asynchronous on the stream). Requires a velocity
+ * model. Errors: STATE (no velocity; receiver buffer full), CUDA. */
+int ws_step(ws_t ws, int nsteps);
+
+/* Copy the traces, [nrec][nt_max] float32, to out. Samples of steps not yet
+ * taken are zero. */
+int ws_read_traces(ws_t ws, float *out, int on_device);
+
+/* Copy u^n (into u) and u^{n-1} (into u_prev) as [nz][ny][nx] float32.
+ * Either pointer may be NULL. */
+int ws_read_field(ws_t ws, float *u, float *u_prev, int on_device);
+
+/* Replace u^n and u^{n-1} (NULL = zero) and set the step counter to step
+ * (t_n = step * dt for the next source sample). Used to restart from a
+ * saved state. */
+int ws_write_field(ws_t ws, const float *u, const float *u_prev, long long step,
+                   int on_device);
+
+/* Number of steps taken since creation (or the last ws_write_field). */
+int ws_get_step(ws_t ws, long long *step);
+
+/* Choose the step kernel (WS_KERNEL_*) and, for WS_KERNEL_STREAM, its tile:
+ * tile_x in {32, 64}, tile_y in {8, 16}, zblock >= 1 planes per CTA
+ * (0 = default). WS_KERNEL_STREAM needs nx + 8 >= tile_x + 8 and
+ * ny >= tile_y; else BADARG. */
+int ws_set_kernel(ws_t ws, int kernel, int tile_x, int tile_y, int zblock);
+
+/* Wait for the stream, then report a device-side failure recorded since the
+ * last call (TIMEOUT when a bounded wait in a kernel ran out). Clears it. */
+int ws_synchronize(ws_t ws);
+
+/* Number of kernel launches issued by this handle since creation. */
+long long ws_launch_count(ws_t ws);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *ws_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WAVESTEP_H */

@@ -1,0 +1,592 @@
+// Host side of the C ABI declared in include/wavestep.h.
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "ws_internal.h"
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+int fail(int code, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+    if (e == cudaErrorMemoryAllocation)
+        return fail(WS_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
+    return fail(WS_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define WS_CUDA(call, what)                              \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+// The 1D weights of the 8th-order second difference, offsets 0..4.
+constexpr double kW0 = -205.0 / 72.0, kW1 = 8.0 / 5.0, kW2 = -1.0 / 5.0, kW3 = 8.0 / 315.0,
+                 kW4 = -1.0 / 560.0;
+
+// Leapfrog stability limit of V dt / h for the 3D 25-point Laplacian: the
+// largest |eigenvalue| times h^2 is 3 (|w0| + 2 sum |wm|) (the checkerboard
+// mode), and the recurrence needs (V dt / h)^2 * that <= 4.
+double cfl_limit() {
+    const double s = std::fabs(kW0) + 2.0 * (std::fabs(kW1) + std::fabs(kW2) + std::fabs(kW3) +
+                                             std::fabs(kW4));
+    return 2.0 / std::sqrt(3.0 * s);
+}
+
+double ricker(double t, double f0, double t0, double amp) {
+    const double pi = 3.14159265358979323846;
+    const double a = pi * f0 * (t - t0);
+    const double a2 = a * a;
+    return amp * (1.0 - 2.0 * a2) * std::exp(-a2);
+}
+
+// Cerjan factor of cell idx on an axis of n cells.
+double taper(int idx, int n, int nb, double a) {
+    const int d = std::min(idx, n - 1 - idx);
+    if (nb <= 0 || d >= nb) return 1.0;
+    const double x = a * double(nb - d);
+    return std::exp(-x * x);
+}
+
+struct SourceDef {
+    int i, j, k;
+    double f0, t0, amp;
+};
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (fn) return fn;
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+        return nullptr;
+    fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    return fn;
+}
+
+}  // namespace
+
+struct ws_handle {
+    ws::Geom g{};
+    double h = 0, dt = 0;
+    float *buf[2] = {nullptr, nullptr};  // the two wavefield levels
+    int cur = 0;                         // buf[cur] = u^n, buf[1-cur] = u^{n-1}
+    float *w = nullptr;                  // (V dt / h)^2, padded
+    float *gx = nullptr, *gy = nullptr, *gz = nullptr;
+    unsigned *status = nullptr;          // [0] status bits, [1] vmax bits, [2] vmin bits
+    cudaStream_t stream = nullptr;
+    bool vel_ok = false;
+    int nb = 0;
+    double a = 0;
+    long long step = 0;
+    std::vector<SourceDef> src;
+
+    int nrec = 0, nt_max = 0;
+    long long trace_start = 0;
+    std::vector<int> rec_ijk;
+    float *traces = nullptr;
+    long long *rec_pidx = nullptr;       // direct path
+    int *rec_ptr = nullptr;              // streaming path: per-tile ranges
+    ws::RecEntry *rec_entries = nullptr;
+    int rec_tiling_tx = 0, rec_tiling_ty = 0;
+
+    int kernel = WS_KERNEL_AUTO;
+    ws::StreamTiling tiling{64, 16, 0};
+    CUtensorMap tmap[2];
+    bool tmap_ok = false;
+    long long launches = 0;
+};
+
+namespace {
+
+size_t field_bytes(const ws::Geom &g) {
+    return size_t(g.pnx) * size_t(g.pny) * size_t(g.pnz) * sizeof(float);
+}
+
+int encode_maps(ws_t ws) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = get_encode_fn();
+    if (!enc) return fail(WS_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+    const ws::Geom &g = ws->g;
+    const int bx = ws->tiling.tx + 2 * ws::kHalo, by = ws->tiling.ty + 2 * ws::kHalo;
+    cuuint64_t dims[3] = {(cuuint64_t)g.pnx, (cuuint64_t)g.pny, (cuuint64_t)g.pnz};
+    cuuint64_t strides[2] = {(cuuint64_t)g.pnx * 4, (cuuint64_t)g.plane * 4};
+    cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    for (int b = 0; b < 2; ++b) {
+        CUresult r = enc(&ws->tmap[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, ws->buf[b], dims,
+                         strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return fail(WS_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    }
+    ws->tmap_ok = true;
+    return WS_OK;
+}
+
+bool stream_fits(const ws_t ws, const ws::StreamTiling &t) {
+    return ws::stream_tiling_supported(t.tx, t.ty) && ws->g.pnx >= t.tx + 2 * ws::kHalo &&
+           ws->g.ny >= t.ty;
+}
+
+int default_zblock(int nz) {
+    const int chunks = std::max(1, (int)std::lround(nz / 128.0));
+    return (nz + chunks - 1) / chunks;
+}
+
+// Choose the kernel for the next steps; fills *tiling for the streaming one.
+int pick_kernel(ws_t ws, ws::StreamTiling *tiling) {
+    if (ws->kernel == WS_KERNEL_DIRECT) return WS_KERNEL_DIRECT;
+    ws::StreamTiling t = ws->tiling;
+    if (ws->kernel == WS_KERNEL_AUTO && !stream_fits(ws, t)) {
+        const ws::StreamTiling cands[3] = {{64, 8, 0}, {32, 16, 0}, {32, 8, 0}};
+        bool found = false;
+        for (const auto &c : cands)
+            if (stream_fits(ws, c)) {
+                t.tx = c.tx;
+                t.ty = c.ty;
+                found = true;
+                break;
+            }
+        if (!found) return WS_KERNEL_DIRECT;
+    }
+    if (t.zb <= 0) t.zb = default_zblock(ws->g.nz);
+    *tiling = t;
+    return WS_KERNEL_STREAM;
+}
+
+void free_receivers(ws_t ws) {
+    cudaFree(ws->traces);
+    cudaFree(ws->rec_pidx);
+    cudaFree(ws->rec_ptr);
+    cudaFree(ws->rec_entries);
+    ws->traces = nullptr;
+    ws->rec_pidx = nullptr;
+    ws->rec_ptr = nullptr;
+    ws->rec_entries = nullptr;
+    ws->rec_tiling_tx = ws->rec_tiling_ty = 0;
+}
+
+// Per-tile receiver table of the streaming kernel for tile t.
+int build_rec_tiles(ws_t ws, const ws::StreamTiling &t) {
+    if (ws->nrec == 0) return WS_OK;
+    if (ws->rec_tiling_tx == t.tx && ws->rec_tiling_ty == t.ty) return WS_OK;
+    const int tiles_x = (ws->g.nx + t.tx - 1) / t.tx;
+    const int tiles_y = (ws->g.ny + t.ty - 1) / t.ty;
+    const int ntiles = tiles_x * tiles_y;
+    std::vector<std::pair<int, ws::RecEntry>> e(ws->nrec);
+    for (int r = 0; r < ws->nrec; ++r) {
+        const int i = ws->rec_ijk[3 * r], j = ws->rec_ijk[3 * r + 1], k = ws->rec_ijk[3 * r + 2];
+        const int tile = (j / t.ty) * tiles_x + (i / t.tx);
+        const int li = i - (i / t.tx) * t.tx, lj = j - (j / t.ty) * t.ty;
+        e[r] = {tile, ws::RecEntry{k, lj * (t.tx / 4) + li / 4, li % 4, r}};
+    }
+    std::stable_sort(e.begin(), e.end(), [](const auto &x, const auto &y) {
+        return x.first != y.first ? x.first < y.first : x.second.k < y.second.k;
+    });
+    std::vector<int> ptr(ntiles + 1, 0);
+    std::vector<ws::RecEntry> ent(ws->nrec);
+    for (int r = 0; r < ws->nrec; ++r) {
+        ptr[e[r].first + 1]++;
+        ent[r] = e[r].second;
+    }
+    for (int tt = 0; tt < ntiles; ++tt) ptr[tt + 1] += ptr[tt];
+    cudaFree(ws->rec_ptr);
+    cudaFree(ws->rec_entries);
+    ws->rec_ptr = nullptr;
+    ws->rec_entries = nullptr;
+    WS_CUDA(cudaMalloc(&ws->rec_ptr, sizeof(int) * (ntiles + 1)), "cudaMalloc receiver table");
+    WS_CUDA(cudaMalloc(&ws->rec_entries, sizeof(ws::RecEntry) * ws->nrec),
+            "cudaMalloc receiver table");
+    WS_CUDA(cudaMemcpyAsync(ws->rec_ptr, ptr.data(), sizeof(int) * (ntiles + 1),
+                            cudaMemcpyHostToDevice, ws->stream),
+            "upload receiver table");
+    WS_CUDA(cudaMemcpyAsync(ws->rec_entries, ent.data(), sizeof(ws::RecEntry) * ws->nrec,
+                            cudaMemcpyHostToDevice, ws->stream),
+            "upload receiver table");
+    // the host vectors die here: wait for the copies
+    WS_CUDA(cudaStreamSynchronize(ws->stream), "upload receiver table");
+    ws->rec_tiling_tx = t.tx;
+    ws->rec_tiling_ty = t.ty;
+    return WS_OK;
+}
+
+// Copy an unpadded [nz][ny][nx] array into the interior of a padded buffer.
+int copy_in(ws_t ws, float *dst, const float *src, int on_device) {
+    const ws::Geom &g = ws->g;
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    for (int k = 0; k < g.nz; ++k) {
+        WS_CUDA(cudaMemcpy2DAsync(dst + ws::pidx(g, 0, 0, k), size_t(g.pnx) * 4,
+                                  src + size_t(k) * g.ny * g.nx, size_t(g.nx) * 4,
+                                  size_t(g.nx) * 4, g.ny, kind, ws->stream),
+                "copy into the padded field");
+    }
+    return WS_OK;
+}
+
+int copy_out(ws_t ws, float *dst, const float *src, int on_device) {
+    const ws::Geom &g = ws->g;
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    for (int k = 0; k < g.nz; ++k) {
+        WS_CUDA(cudaMemcpy2DAsync(dst + size_t(k) * g.ny * g.nx, size_t(g.nx) * 4,
+                                  src + ws::pidx(g, 0, 0, k), size_t(g.pnx) * 4,
+                                  size_t(g.nx) * 4, g.ny, kind, ws->stream),
+                "copy out of the padded field");
+    }
+    return WS_OK;
+}
+
+int upload_profiles(ws_t ws) {
+    const ws::Geom &g = ws->g;
+    std::vector<float> px(g.nx), py(g.ny), pz(g.nz);
+    for (int i = 0; i < g.nx; ++i) px[i] = (float)taper(i, g.nx, ws->nb, ws->a);
+    for (int j = 0; j < g.ny; ++j) py[j] = (float)taper(j, g.ny, ws->nb, ws->a);
+    for (int k = 0; k < g.nz; ++k) pz[k] = (float)taper(k, g.nz, ws->nb, ws->a);
+    WS_CUDA(cudaMemcpyAsync(ws->gx, px.data(), 4 * px.size(), cudaMemcpyHostToDevice, ws->stream),
+            "upload taper");
+    WS_CUDA(cudaMemcpyAsync(ws->gy, py.data(), 4 * py.size(), cudaMemcpyHostToDevice, ws->stream),
+            "upload taper");
+    WS_CUDA(cudaMemcpyAsync(ws->gz, pz.data(), 4 * pz.size(), cudaMemcpyHostToDevice, ws->stream),
+            "upload taper");
+    WS_CUDA(cudaStreamSynchronize(ws->stream), "upload taper");
+    return WS_OK;
+}
+
+void destroy(ws_t ws) {
+    if (!ws) return;
+    cudaStreamSynchronize(ws->stream);
+    cudaFree(ws->buf[0]);
+    cudaFree(ws->buf[1]);
+    cudaFree(ws->w);
+    cudaFree(ws->gx);
+    cudaFree(ws->gy);
+    cudaFree(ws->gz);
+    cudaFree(ws->status);
+    free_receivers(ws);
+    delete ws;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *ws_last_error(void) { return g_err; }
+
+int ws_create(ws_t *out, int nx, int ny, int nz, double h, double dt) {
+    if (!out) return fail(WS_ERR_BADARG, "ws_create: out is NULL");
+    *out = nullptr;
+    if (nx < 1 || ny < 1 || nz < 1 || nx > 65535 || ny > 65535 || nz > 65535)
+        return fail(WS_ERR_BADARG, "ws_create: sizes must be in [1, 65535], got %d x %d x %d", nx,
+                    ny, nz);
+    if (!(h > 0.0) || !(dt > 0.0) || !std::isfinite(h) || !std::isfinite(dt))
+        return fail(WS_ERR_BADARG, "ws_create: h and dt must be finite and > 0");
+    ws_t ws = new (std::nothrow) ws_handle();
+    if (!ws) return fail(WS_ERR_OOM, "ws_create: host allocation failed");
+    ws::Geom &g = ws->g;
+    g.nx = nx;
+    g.ny = ny;
+    g.nz = nz;
+    g.pnx = ((nx + 2 * ws::kHalo) + 3) / 4 * 4;
+    g.pny = ny + 2 * ws::kHalo;
+    g.pnz = nz + 2 * ws::kHalo;
+    g.plane = (long long)g.pnx * g.pny;
+    ws->h = h;
+    ws->dt = dt;
+    const size_t fb = field_bytes(g);
+    cudaError_t e = cudaSuccess;
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b) e = cudaMalloc(&ws->buf[b], fb);
+    if (e == cudaSuccess) e = cudaMalloc(&ws->w, fb);
+    if (e == cudaSuccess) e = cudaMalloc(&ws->gx, sizeof(float) * nx);
+    if (e == cudaSuccess) e = cudaMalloc(&ws->gy, sizeof(float) * ny);
+    if (e == cudaSuccess) e = cudaMalloc(&ws->gz, sizeof(float) * nz);
+    if (e == cudaSuccess) e = cudaMalloc(&ws->status, sizeof(unsigned) * 4);
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b) e = cudaMemsetAsync(ws->buf[b], 0, fb, ws->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ws->w, 0, fb, ws->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ws->status, 0, sizeof(unsigned) * 4, ws->stream);
+    if (e != cudaSuccess) {
+        destroy(ws);
+        return cuda_fail(e, "ws_create");
+    }
+    int rc = upload_profiles(ws);
+    if (rc == WS_OK) rc = encode_maps(ws);
+    if (rc == WS_OK && cudaStreamSynchronize(ws->stream) != cudaSuccess)
+        rc = cuda_fail(cudaGetLastError(), "ws_create");
+    if (rc != WS_OK) {
+        destroy(ws);
+        return rc;
+    }
+    *out = ws;
+    return WS_OK;
+}
+
+int ws_destroy(ws_t ws) {
+    destroy(ws);
+    return WS_OK;
+}
+
+int ws_set_stream(ws_t ws, void *cuda_stream) {
+    if (!ws) return fail(WS_ERR_BADARG, "ws_set_stream: NULL handle");
+    WS_CUDA(cudaStreamSynchronize(ws->stream), "ws_set_stream");
+    ws->stream = static_cast<cudaStream_t>(cuda_stream);
+    return WS_OK;
+}
+
+int ws_set_velocity(ws_t ws, const float *v, int on_device) {
+    if (!ws || !v) return fail(WS_ERR_BADARG, "ws_set_velocity: NULL argument");
+    ws->vel_ok = false;
+    int rc = copy_in(ws, ws->w, v, on_device);
+    if (rc != WS_OK) return rc;
+    static const unsigned init[2] = {0u, 0x7f800000u};
+    WS_CUDA(cudaMemcpyAsync(ws->status + 1, init, sizeof init, cudaMemcpyHostToDevice, ws->stream),
+            "ws_set_velocity");
+    WS_CUDA(ws::launch_velocity_to_w(ws->w, ws->g, ws->dt / ws->h, ws->status + 1, ws->stream),
+            "velocity conversion kernel");
+    ws->launches++;
+    unsigned ext[2];
+    WS_CUDA(cudaMemcpyAsync(ext, ws->status + 1, sizeof ext, cudaMemcpyDeviceToHost, ws->stream),
+            "ws_set_velocity");
+    WS_CUDA(cudaStreamSynchronize(ws->stream), "ws_set_velocity");
+    float vmax, vmin;
+    std::memcpy(&vmax, &ext[0], 4);
+    std::memcpy(&vmin, &ext[1], 4);
+    if (ext[1] == 0u) return fail(WS_ERR_BADARG, "ws_set_velocity: every value must be finite and > 0");
+    const double c = double(vmax) * ws->dt / ws->h;
+    if (c > cfl_limit())
+        return fail(WS_ERR_CFL, "ws_set_velocity: max(V) dt / h = %.6f exceeds the limit %.6f", c,
+                    cfl_limit());
+    ws->vel_ok = true;
+    return WS_OK;
+}
+
+int ws_set_sponge(ws_t ws, int nb, double a) {
+    if (!ws) return fail(WS_ERR_BADARG, "ws_set_sponge: NULL handle");
+    if (nb < 0 || !(a >= 0.0) || !std::isfinite(a))
+        return fail(WS_ERR_BADARG, "ws_set_sponge: need nb >= 0 and finite a >= 0");
+    ws->nb = nb;
+    ws->a = a;
+    return upload_profiles(ws);
+}
+
+int ws_add_source(ws_t ws, int ix, int iy, int iz, double f0, double t0, double amp) {
+    if (!ws) return fail(WS_ERR_BADARG, "ws_add_source: NULL handle");
+    const ws::Geom &g = ws->g;
+    if (ix < 0 || ix >= g.nx || iy < 0 || iy >= g.ny || iz < 0 || iz >= g.nz)
+        return fail(WS_ERR_BADARG, "ws_add_source: cell (%d, %d, %d) outside the grid", ix, iy, iz);
+    if (!(f0 > 0.0) || !std::isfinite(f0) || !std::isfinite(t0) || !std::isfinite(amp))
+        return fail(WS_ERR_BADARG, "ws_add_source: need finite t0, amp and f0 > 0");
+    if ((int)ws->src.size() >= ws::kMaxSources)
+        return fail(WS_ERR_BADARG, "ws_add_source: at most %d sources", ws::kMaxSources);
+    ws->src.push_back({ix, iy, iz, f0, t0, amp});
+    return WS_OK;
+}
+
+int ws_clear_sources(ws_t ws) {
+    if (!ws) return fail(WS_ERR_BADARG, "ws_clear_sources: NULL handle");
+    ws->src.clear();
+    return WS_OK;
+}
+
+int ws_set_receivers(ws_t ws, int nrec, const int *ijk, int nt_max) {
+    if (!ws) return fail(WS_ERR_BADARG, "ws_set_receivers: NULL handle");
+    if (nrec < 0 || (nrec > 0 && (!ijk || nt_max < 1)))
+        return fail(WS_ERR_BADARG, "ws_set_receivers: need nrec >= 0, ijk and nt_max >= 1");
+    const ws::Geom &g = ws->g;
+    for (int r = 0; r < nrec; ++r) {
+        const int i = ijk[3 * r], j = ijk[3 * r + 1], k = ijk[3 * r + 2];
+        if (i < 0 || i >= g.nx || j < 0 || j >= g.ny || k < 0 || k >= g.nz)
+            return fail(WS_ERR_BADARG, "ws_set_receivers: receiver %d at (%d, %d, %d) outside the grid",
+                        r, i, j, k);
+    }
+    if (nrec > 0 && (long long)nrec * nt_max > (1ll << 40))
+        return fail(WS_ERR_BADARG, "ws_set_receivers: trace buffer too large");
+    WS_CUDA(cudaStreamSynchronize(ws->stream), "ws_set_receivers");
+    free_receivers(ws);
+    ws->nrec = 0;
+    ws->nt_max = 0;
+    ws->rec_ijk.assign(ijk, ijk + 3 * size_t(nrec));
+    ws->trace_start = ws->step;
+    if (nrec == 0) return WS_OK;
+    WS_CUDA(cudaMalloc(&ws->traces, sizeof(float) * size_t(nrec) * nt_max), "cudaMalloc traces");
+    WS_CUDA(cudaMemsetAsync(ws->traces, 0, sizeof(float) * size_t(nrec) * nt_max, ws->stream),
+            "zero traces");
+    std::vector<long long> pid(nrec);
+    for (int r = 0; r < nrec; ++r) pid[r] = ws::pidx(g, ijk[3 * r], ijk[3 * r + 1], ijk[3 * r + 2]);
+    WS_CUDA(cudaMalloc(&ws->rec_pidx, sizeof(long long) * nrec), "cudaMalloc receivers");
+    WS_CUDA(cudaMemcpyAsync(ws->rec_pidx, pid.data(), sizeof(long long) * nrec,
+                            cudaMemcpyHostToDevice, ws->stream),
+            "upload receivers");
+    WS_CUDA(cudaStreamSynchronize(ws->stream), "upload receivers");
+    ws->nrec = nrec;
+    ws->nt_max = nt_max;
+    return WS_OK;
+}
+
+int ws_set_kernel(ws_t ws, int kernel, int tile_x, int tile_y, int zblock) {
+    if (!ws) return fail(WS_ERR_BADARG, "ws_set_kernel: NULL handle");
+    if (kernel != WS_KERNEL_AUTO && kernel != WS_KERNEL_DIRECT && kernel != WS_KERNEL_STREAM)
+        return fail(WS_ERR_BADARG, "ws_set_kernel: unknown kernel %d", kernel);
+    if (zblock < 0) return fail(WS_ERR_BADARG, "ws_set_kernel: zblock must be >= 0");
+    ws::StreamTiling t = ws->tiling;
+    if (tile_x != 0 || tile_y != 0) {
+        if (!ws::stream_tiling_supported(tile_x, tile_y))
+            return fail(WS_ERR_BADARG, "ws_set_kernel: unsupported tile %d x %d", tile_x, tile_y);
+        t.tx = tile_x;
+        t.ty = tile_y;
+    }
+    t.zb = zblock;
+    if (kernel == WS_KERNEL_STREAM && !stream_fits(ws, t))
+        return fail(WS_ERR_BADARG, "ws_set_kernel: grid %d x %d is smaller than the tile %d x %d",
+                    ws->g.nx, ws->g.ny, t.tx, t.ty);
+    const bool box_changed = t.tx != ws->tiling.tx || t.ty != ws->tiling.ty;
+    ws->kernel = kernel;
+    ws->tiling = t;
+    if (box_changed) return encode_maps(ws);
+    return WS_OK;
+}
+
+int ws_step(ws_t ws, int nsteps) {
+    if (!ws) return fail(WS_ERR_BADARG, "ws_step: NULL handle");
+    if (nsteps < 0) return fail(WS_ERR_BADARG, "ws_step: nsteps must be >= 0");
+    if (!ws->vel_ok) return fail(WS_ERR_STATE, "ws_step: no valid velocity model");
+    if (ws->nrec > 0) {
+        const long long col = ws->step - ws->trace_start;
+        if (col < 0 || col + nsteps > ws->nt_max)
+            return fail(WS_ERR_STATE,
+                        "ws_step: receivers hold %d steps from step %lld; cannot record steps "
+                        "%lld..%lld",
+                        ws->nt_max, ws->trace_start, ws->step, ws->step + nsteps - 1);
+    }
+    ws::StreamTiling tiling{};
+    const int kern = pick_kernel(ws, &tiling);
+    if (kern == WS_KERNEL_STREAM) {
+        if (tiling.tx != ws->tiling.tx || tiling.ty != ws->tiling.ty) {
+            ws->tiling.tx = tiling.tx;
+            ws->tiling.ty = tiling.ty;
+            int rc = encode_maps(ws);
+            if (rc != WS_OK) return rc;
+        }
+        int rc = build_rec_tiles(ws, tiling);
+        if (rc != WS_OK) return rc;
+    }
+    ws::StepArgs a{};
+    a.g = ws->g;
+    const double h2 = ws->h * ws->h;
+    a.c.c0x3 = (float)(3.0 * kW0);
+    a.c.c1 = (float)kW1;
+    a.c.c2 = (float)kW2;
+    a.c.c3 = (float)kW3;
+    a.c.c4 = (float)kW4;
+    a.gx = ws->gx;
+    a.gy = ws->gy;
+    a.gz = ws->gz;
+    a.traces = ws->traces;
+    a.nt_max = ws->nt_max;
+    a.status = ws->status;
+    a.src.n = (int)ws->src.size();
+    for (int s = 0; s < nsteps; ++s) {
+        const double t = double(ws->step) * ws->dt;
+        for (int q = 0; q < a.src.n; ++q) {
+            const SourceDef &d = ws->src[q];
+            a.src.s[q] = ws::SourceSample{d.i, d.j, d.k, (float)(h2 * ricker(t, d.f0, d.t0, d.amp))};
+        }
+        a.trace_step = ws->step - ws->trace_start;
+        float *u = ws->buf[ws->cur];
+        float *up = ws->buf[1 - ws->cur];
+        cudaError_t e;
+        if (kern == WS_KERNEL_STREAM) {
+            e = ws::launch_step_stream(&ws->tmap[ws->cur], u, up, ws->w, a, tiling,
+                                       ws->nrec > 0 ? ws->rec_ptr : nullptr, ws->rec_entries,
+                                       ws->stream);
+            ws->launches++;
+        } else {
+            e = ws::launch_step_direct(u, up, ws->w, a, ws->stream);
+            ws->launches++;
+            if (e == cudaSuccess && ws->nrec > 0) {
+                e = ws::launch_gather_receivers(up, ws->rec_pidx, ws->nrec, ws->traces, ws->nt_max,
+                                                a.trace_step, ws->stream);
+                ws->launches++;
+            }
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "ws_step launch");
+        ws->cur = 1 - ws->cur;
+        ws->step++;
+    }
+    return WS_OK;
+}
+
+int ws_read_traces(ws_t ws, float *out, int on_device) {
+    if (!ws || !out) return fail(WS_ERR_BADARG, "ws_read_traces: NULL argument");
+    if (ws->nrec == 0) return WS_OK;
+    WS_CUDA(cudaMemcpyAsync(out, ws->traces, sizeof(float) * size_t(ws->nrec) * ws->nt_max,
+                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                            ws->stream),
+            "ws_read_traces");
+    if (!on_device) WS_CUDA(cudaStreamSynchronize(ws->stream), "ws_read_traces");
+    return WS_OK;
+}
+
+int ws_read_field(ws_t ws, float *u, float *u_prev, int on_device) {
+    if (!ws) return fail(WS_ERR_BADARG, "ws_read_field: NULL handle");
+    int rc = WS_OK;
+    if (u) rc = copy_out(ws, u, ws->buf[ws->cur], on_device);
+    if (rc == WS_OK && u_prev) rc = copy_out(ws, u_prev, ws->buf[1 - ws->cur], on_device);
+    if (rc != WS_OK) return rc;
+    if (!on_device) WS_CUDA(cudaStreamSynchronize(ws->stream), "ws_read_field");
+    return WS_OK;
+}
+
+int ws_write_field(ws_t ws, const float *u, const float *u_prev, long long step, int on_device) {
+    if (!ws) return fail(WS_ERR_BADARG, "ws_write_field: NULL handle");
+    if (step < 0) return fail(WS_ERR_BADARG, "ws_write_field: step must be >= 0");
+    const size_t fb = field_bytes(ws->g);
+    float *dst[2] = {ws->buf[ws->cur], ws->buf[1 - ws->cur]};
+    const float *srcs[2] = {u, u_prev};
+    for (int b = 0; b < 2; ++b) {
+        WS_CUDA(cudaMemsetAsync(dst[b], 0, fb, ws->stream), "ws_write_field");
+        if (srcs[b]) {
+            int rc = copy_in(ws, dst[b], srcs[b], on_device);
+            if (rc != WS_OK) return rc;
+        }
+    }
+    if (!on_device) WS_CUDA(cudaStreamSynchronize(ws->stream), "ws_write_field");
+    ws->step = step;
+    return WS_OK;
+}
+
+int ws_get_step(ws_t ws, long long *step) {
+    if (!ws || !step) return fail(WS_ERR_BADARG, "ws_get_step: NULL argument");
+    *step = ws->step;
+    return WS_OK;
+}
+
+int ws_synchronize(ws_t ws) {
+    if (!ws) return fail(WS_ERR_BADARG, "ws_synchronize: NULL handle");
+    WS_CUDA(cudaStreamSynchronize(ws->stream), "ws_synchronize");
+    unsigned st = 0;
+    WS_CUDA(cudaMemcpy(&st, ws->status, sizeof st, cudaMemcpyDeviceToHost), "ws_synchronize");
+    if (st & ws::kStatusTimeout) {
+        WS_CUDA(cudaMemset(ws->status, 0, sizeof(unsigned)), "ws_synchronize");
+        return fail(WS_ERR_TIMEOUT, "a bounded device wait ran out in a step kernel");
+    }
+    return WS_OK;
+}
+
+long long ws_launch_count(ws_t ws) { return ws ? ws->launches : -1; }
+
+}  // extern "C"

@@ -1,0 +1,91 @@
+// Internal declarations shared by the translation units of libwavestep.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+
+#include "wavestep.h"
+
+namespace ws {
+
+constexpr int kHalo = 4;                 // four neighbours per side (Section II)
+constexpr int kMaxSources = WS_MAX_SOURCES;
+
+// Bits of the device status word.
+constexpr unsigned kStatusTimeout = 1u;
+
+// Bounded device waits give up after this many nanoseconds of %globaltimer.
+constexpr unsigned long long kWaitLimitNs = 1000000000ull;
+
+// Stencil weights of the 8th-order second difference (offsets 0..4), the
+// centre one already multiplied by 3 (one per axis, Section III-C-2).
+struct Coeffs {
+    float c0x3, c1, c2, c3, c4;
+};
+
+// Per-launch source samples: cell and (h^2 * s(t_n)); the kernel multiplies
+// by the stored (V dt / h)^2 of the cell, which gives (V dt)^2 s(t_n).
+struct SourceSample {
+    int i, j, k;
+    float amp;
+};
+struct Sources {
+    int n;
+    SourceSample s[kMaxSources];
+};
+
+// Geometry of the padded fields: [pnz][pny][pnx], interior (i,j,k) at
+// padded (i+4, j+4, k+4); pnx is a multiple of 4 so rows are 16-byte aligned.
+struct Geom {
+    int nx, ny, nz;
+    int pnx, pny, pnz;
+    long long plane;  // pnx * pny
+};
+
+__host__ __device__ inline long long pidx(const Geom &g, int i, int j, int k) {
+    return ((long long)(k + kHalo) * g.pny + (j + kHalo)) * g.pnx + (i + kHalo);
+}
+
+// Receivers grouped for the streaming kernel: per xy tile a contiguous range
+// of entries sorted by k. owner = thread index inside the tile's CTA,
+// lane = which of the thread's 4 x-cells, slot = receiver number r.
+struct RecEntry {
+    int k;
+    int owner;
+    int lane;
+    int r;
+};
+
+struct StepArgs {
+    Geom g;
+    Coeffs c;
+    Sources src;
+    const float *gx, *gy, *gz;   // taper profiles (1.0 without damping)
+    float *traces;               // [nrec][nt_max] or null
+    int nt_max;
+    long long trace_step;        // column of this step in traces
+    unsigned *status;            // device status word
+};
+
+// Launchers (stream-ordered, no synchronization).
+cudaError_t launch_step_direct(const float *u, float *up, const float *w, const StepArgs &a,
+                               cudaStream_t s);
+cudaError_t launch_gather_receivers(const float *u_next, const long long *rec_pidx, int nrec,
+                                    float *traces, int nt_max, long long trace_step,
+                                    cudaStream_t s);
+cudaError_t launch_velocity_to_w(float *w, const Geom &g, double dt_over_h,
+                                 unsigned *extrema /* [2]: max bits, min bits */,
+                                 cudaStream_t s);
+
+struct StreamTiling {
+    int tx, ty, zb;
+};
+bool stream_tiling_supported(int tx, int ty);
+cudaError_t launch_step_stream(const CUtensorMap *tmap_u, const float *u, float *up,
+                               const float *w, const StepArgs &a, const StreamTiling &t,
+                               const int *rec_ptr, const RecEntry *rec, cudaStream_t s);
+size_t stream_smem_bytes(const StreamTiling &t);
+
+}  // namespace ws

@@ -1,0 +1,122 @@
+"""Seeded synthetic workloads shared by the tests, the benchmark and the oracle runs.
+
+This module only builds inputs (velocity models, cell positions, time-step
+sizes, sizes of grids); it holds none of the stepper's arithmetic, and it
+imports neither the CUDA binding nor the oracle. The same arrays are fed to
+both sides.
+
+Workloads (shapes and value ranges of the paper's setting: synthetic grids of
+hundreds to a thousand cells per axis, 1000 steps, Section IV):
+
+* ``homogeneous_cube`` -- 64^3, h = 10 m, v = 2000 m/s, dt at CFL 0.4,
+  100 steps, 15 Hz Ricker at the centre, 16 receivers (4 x 4) on the top plane,
+  no damping.
+* ``layered_model`` -- 10 horizontal layers of equal thickness, layer l at
+  1500 + l * 3000 / 9 m/s, times (1 + 0.05 n) with n a smooth noise field in
+  [-1, 1], clipped to [1500, 4500] m/s. n is seeded N(0, 1) noise on a coarse
+  grid of spacing 8 cells, Gaussian-filtered (sigma = 1 coarse cell, i.e.
+  8 fine cells) and trilinearly interpolated to the grid.
+* ``layered_survey`` -- the layered model with a 20-cell absorbing layer on
+  every face, dt at CFL 0.4, one 10 Hz Ricker at (nx/2, ny/2, 20) and a
+  32 x 32 receiver grid on the plane k = 20; 1024^3 and 1000 steps is the
+  benchmark's workload, smaller sizes are parity cases.
+"""
+
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+CFL = 0.4
+
+
+@dataclass
+class Workload:
+    name: str
+    nx: int
+    ny: int
+    nz: int
+    h: float
+    dt: float
+    nt: int
+    vel: np.ndarray                      # [nz][ny][nx] float32, m/s
+    sources: list = field(default_factory=list)   # (i, j, k, f0, t0, amp)
+    receivers: np.ndarray = None         # [nrec][3] int32 (i, j, k)
+    sponge: tuple = (0, 0.0)             # (nb, a)
+
+    @property
+    def points(self) -> int:
+        return self.nx * self.ny * self.nz
+
+
+def cfl_dt(vmax: float, h: float, cfl: float = CFL) -> float:
+    """Time step with vmax * dt / h = cfl."""
+    return cfl * h / float(vmax)
+
+
+def homogeneous_cube(n: int = 64, nt: int = 100, h: float = 10.0, v: float = 2000.0,
+                     f0: float = 15.0) -> Workload:
+    vel = np.full((n, n, n), v, dtype=np.float32)
+    c = n // 2
+    rec = np.array([[int((p + 0.5) * n / 4), int((q + 0.5) * n / 4), 0]
+                    for q in range(4) for p in range(4)], dtype=np.int32)
+    return Workload("homogeneous_cube", n, n, n, h, cfl_dt(v, h), nt, vel,
+                    sources=[(c, c, c, f0, 1.0 / f0, 1.0)], receivers=rec, sponge=(0, 0.0))
+
+
+def smooth_noise(shape, seed: int, spacing: int = 8) -> np.ndarray:
+    """Smooth field in [-1, 1]: coarse Gaussian-filtered noise, trilinear upsampling."""
+    import torch
+    from scipy.ndimage import gaussian_filter
+
+    nz, ny, nx = shape
+    cshape = tuple(max(2, -(-n // spacing) + 1) for n in (nz, ny, nx))
+    rng = np.random.Generator(np.random.PCG64(seed))
+    coarse = gaussian_filter(rng.standard_normal(cshape), sigma=1.0, mode="wrap")
+    coarse /= np.abs(coarse).max()
+    t = torch.from_numpy(coarse.astype(np.float32))[None, None]
+    # coarse node c sits at fine cell c * spacing; sample the fine grid inside
+    size = tuple((m - 1) * spacing + 1 for m in cshape)
+    fine = torch.nn.functional.interpolate(t, size=size, mode="trilinear", align_corners=True)
+    return fine[0, 0, :nz, :ny, :nx].contiguous().numpy()
+
+
+def layered_model(nx: int, ny: int, nz: int, seed: int = 2204, layers: int = 10,
+                  vmin: float = 1500.0, vmax: float = 4500.0, noise: float = 0.05) -> np.ndarray:
+    k = np.arange(nz)
+    layer = np.minimum(k * layers // nz, layers - 1)
+    base = (vmin + layer * (vmax - vmin) / (layers - 1)).astype(np.float32)
+    n = smooth_noise((nz, ny, nx), seed)
+    vel = n
+    vel *= np.float32(noise)
+    vel += np.float32(1.0)
+    vel *= base[:, None, None]
+    np.clip(vel, vmin, vmax, out=vel)
+    return vel
+
+
+def surface_receivers(nx: int, ny: int, k: int, side: int, margin: int) -> np.ndarray:
+    """side x side grid on plane k, evenly spread inside [margin, n - margin)."""
+    ii = [margin + int((p + 0.5) * (nx - 2 * margin) / side) for p in range(side)]
+    jj = [margin + int((q + 0.5) * (ny - 2 * margin) / side) for q in range(side)]
+    return np.array([[i, j, k] for j in jj for i in ii], dtype=np.int32)
+
+
+def layered_survey(nx: int = 1024, ny: int = 1024, nz: int = 1024, nt: int = 1000,
+                   h: float = 10.0, nb: int = 20, a: float = 0.015, f0: float = 10.0,
+                   side: int = 32, seed: int = 2204) -> Workload:
+    vel = layered_model(nx, ny, nz, seed=seed)
+    dt = cfl_dt(float(vel.max()), h)
+    src = [(nx // 2, ny // 2, min(nb, nz - 1), f0, 1.0 / f0, 1.0)]
+    rec = surface_receivers(nx, ny, min(nb, nz - 1), min(side, nx, ny), min(nb, nx // 4, ny // 4))
+    return Workload(f"layered_survey_{nx}x{ny}x{nz}", nx, ny, nz, h, dt, nt, vel,
+                    sources=src, receivers=rec, sponge=(nb, a))
+
+
+def smooth_random_velocity(shape, seed: int, vmin: float = 1500.0, vmax: float = 4500.0,
+                           spacing: int = 4) -> np.ndarray:
+    """Smooth random model spanning [vmin, vmax] (per-test or per-shot models)."""
+    n = smooth_noise(shape, seed, spacing=spacing)
+    v = 0.5 * (vmin + vmax) + 0.5 * (vmax - vmin) * n
+    return np.clip(v, vmin, vmax).astype(np.float32)
