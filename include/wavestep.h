@@ -31,7 +31,8 @@
  *    that stream before returning; the others are asynchronous.
  *  - A handle is not thread-safe; distinct handles are independent.
  *  - Device memory: the handle allocates (cudaMalloc) three padded fields of
- *    (nx+8 rounded up to 4) * (ny+8) * (nz+8) floats plus O(nx+ny+nz) and the
+ *    P * (ny+8) * (nz+8) floats, P = 32 + nx + 4 rounded up to a multiple of
+ *    32 (interior rows start on 128-byte lines), plus O(nx+ny+nz) and the
  *    trace buffer; ws_destroy frees them.
  */
 #ifndef WAVESTEP_H
@@ -132,8 +133,8 @@ int ws_get_step(ws_t ws, long long *step);
 
 /* Choose the step kernel (WS_KERNEL_*) and, for WS_KERNEL_STREAM, its tile:
  * tile_x in {32, 64}, tile_y in {8, 16}, zblock >= 1 planes per CTA
- * (0 = default). WS_KERNEL_STREAM needs nx + 8 >= tile_x + 8 and
- * ny >= tile_y; else BADARG. */
+ * (0 = default). WS_KERNEL_STREAM needs nx >= tile_x and ny >= tile_y;
+ * else BADARG. */
 int ws_set_kernel(ws_t ws, int kernel, int tile_x, int tile_y, int zblock);
 
 /* Wait for the stream, then report a device-side failure recorded since the

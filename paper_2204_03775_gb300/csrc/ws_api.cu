@@ -108,8 +108,10 @@ struct ws_handle {
     int rec_tiling_tx = 0, rec_tiling_ty = 0;
 
     int kernel = WS_KERNEL_AUTO;
-    ws::StreamTiling tiling{64, 16, 0};
-    CUtensorMap tmap[2];
+    ws::StreamTiling tiling{64, 8, 0};
+    CUtensorMap tmap_halo[2];  // buf[b] with the (tx+8, ty+8, 1) box
+    CUtensorMap tmap_tile[2];  // buf[b] with the (tx, ty, 1) box
+    CUtensorMap tmap_w;        // w with the (tx, ty, 1) box
     bool tmap_ok = false;
     long long launches = 0;
 };
@@ -120,29 +122,35 @@ size_t field_bytes(const ws::Geom &g) {
     return size_t(g.pnx) * size_t(g.pny) * size_t(g.pnz) * sizeof(float);
 }
 
-int encode_maps(ws_t ws) {
+int encode_map(CUtensorMap *map, void *base, const ws::Geom &g, int bx, int by) {
     PFN_cuTensorMapEncodeTiled_v12000 enc = get_encode_fn();
     if (!enc) return fail(WS_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
-    const ws::Geom &g = ws->g;
-    const int bx = ws->tiling.tx + 2 * ws::kHalo, by = ws->tiling.ty + 2 * ws::kHalo;
     cuuint64_t dims[3] = {(cuuint64_t)g.pnx, (cuuint64_t)g.pny, (cuuint64_t)g.pnz};
     cuuint64_t strides[2] = {(cuuint64_t)g.pnx * 4, (cuuint64_t)g.plane * 4};
     cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 1};
     cuuint32_t estr[3] = {1, 1, 1};
-    for (int b = 0; b < 2; ++b) {
-        CUresult r = enc(&ws->tmap[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, ws->buf[b], dims,
-                         strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-        if (r != CUDA_SUCCESS) return fail(WS_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
-    }
-    ws->tmap_ok = true;
+    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(WS_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
     return WS_OK;
 }
 
+int encode_maps(ws_t ws) {
+    const ws::Geom &g = ws->g;
+    const int tx = ws->tiling.tx, ty = ws->tiling.ty;
+    int rc = WS_OK;
+    for (int b = 0; b < 2 && rc == WS_OK; ++b) {
+        rc = encode_map(&ws->tmap_halo[b], ws->buf[b], g, tx + 2 * ws::kHalo, ty + 2 * ws::kHalo);
+        if (rc == WS_OK) rc = encode_map(&ws->tmap_tile[b], ws->buf[b], g, tx, ty);
+    }
+    if (rc == WS_OK) rc = encode_map(&ws->tmap_w, ws->w, g, tx, ty);
+    ws->tmap_ok = rc == WS_OK;
+    return rc;
+}
+
 bool stream_fits(const ws_t ws, const ws::StreamTiling &t) {
-    return ws::stream_tiling_supported(t.tx, t.ty) && ws->g.pnx >= t.tx + 2 * ws::kHalo &&
-           ws->g.ny >= t.ty;
+    return ws::stream_tiling_supported(t.tx, t.ty) && ws->g.nx >= t.tx && ws->g.ny >= t.ty;
 }
 
 int default_zblock(int nz) {
@@ -155,7 +163,7 @@ int pick_kernel(ws_t ws, ws::StreamTiling *tiling) {
     if (ws->kernel == WS_KERNEL_DIRECT) return WS_KERNEL_DIRECT;
     ws::StreamTiling t = ws->tiling;
     if (ws->kernel == WS_KERNEL_AUTO && !stream_fits(ws, t)) {
-        const ws::StreamTiling cands[3] = {{64, 8, 0}, {32, 16, 0}, {32, 8, 0}};
+        const ws::StreamTiling cands[3] = {{32, 16, 0}, {64, 16, 0}, {32, 8, 0}};
         bool found = false;
         for (const auto &c : cands)
             if (stream_fits(ws, c)) {
@@ -302,7 +310,7 @@ int ws_create(ws_t *out, int nx, int ny, int nz, double h, double dt) {
     g.nx = nx;
     g.ny = ny;
     g.nz = nz;
-    g.pnx = ((nx + 2 * ws::kHalo) + 3) / 4 * 4;
+    g.pnx = (ws::kXOff + nx + ws::kHalo + ws::kRowAlign - 1) / ws::kRowAlign * ws::kRowAlign;
     g.pny = ny + 2 * ws::kHalo;
     g.pnz = nz + 2 * ws::kHalo;
     g.plane = (long long)g.pnx * g.pny;
@@ -510,7 +518,8 @@ int ws_step(ws_t ws, int nsteps) {
         float *up = ws->buf[1 - ws->cur];
         cudaError_t e;
         if (kern == WS_KERNEL_STREAM) {
-            e = ws::launch_step_stream(&ws->tmap[ws->cur], u, up, ws->w, a, tiling,
+            e = ws::launch_step_stream(&ws->tmap_halo[ws->cur], &ws->tmap_tile[1 - ws->cur],
+                                       &ws->tmap_w, up, a, tiling,
                                        ws->nrec > 0 ? ws->rec_ptr : nullptr, ws->rec_entries,
                                        ws->stream);
             ws->launches++;
