@@ -53,7 +53,7 @@ extern "C" {
 /* Step kernels selectable with ws_set_kernel. */
 #define WS_KERNEL_AUTO    0  /* the streaming kernel when the grid fits its tile, else DIRECT */
 #define WS_KERNEL_DIRECT  1  /* one thread per cell, neighbours loaded from global memory */
-#define WS_KERNEL_STREAM  2  /* z-streaming: TMA-staged xy tiles + 9-plane register queue */
+#define WS_KERNEL_STREAM  2  /* z-streaming: TMA rings + 9-plane register queue, persistent */
 
 #define WS_MAX_SOURCES   16
 
@@ -132,8 +132,9 @@ int ws_write_field(ws_t ws, const float *u, const float *u_prev, long long step,
 int ws_get_step(ws_t ws, long long *step);
 
 /* Choose the step kernel (WS_KERNEL_*) and, for WS_KERNEL_STREAM, its tile:
- * tile_x in {32, 64}, tile_y in {8, 16}, zblock >= 1 planes per CTA
- * (0 = default). WS_KERNEL_STREAM needs nx >= tile_x and ny >= tile_y;
+ * tile_x x tile_y in {32x8, 32x16, 64x8, 64x16, 64x32} (0, 0 = keep the
+ * current tile; the default is 32x16), zblock >= 1 planes per work item
+ * (0 = default, about 128). WS_KERNEL_STREAM needs nx >= tile_x and ny >= tile_y;
  * else BADARG. */
 int ws_set_kernel(ws_t ws, int kernel, int tile_x, int tile_y, int zblock);
 

@@ -104,6 +104,5 @@ cudaError_t launch_step_stream(const CUtensorMap *tmap_u, const CUtensorMap *tma
                                const CUtensorMap *tmap_w, float *up, const StepArgs &a,
                                const StreamTiling &t, const int *rec_ptr, const RecEntry *rec,
                                cudaStream_t s);
-size_t stream_smem_bytes(const StreamTiling &t);
 
 }  // namespace ws

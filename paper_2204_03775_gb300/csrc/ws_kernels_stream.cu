@@ -1,28 +1,25 @@
 // Streaming step kernel for sm_103a: the hot path of the library.
 //
-// Each CTA owns a TX x TY tile of (x, y) columns and a block of zb planes,
-// which it walks in increasing z. The paper keeps a whole z column in a
-// processing element's memory and receives x/y neighbours from 4 PEs per
-// direction over the fabric (Section III-B, III-C); here the column lives in
-// a per-thread register queue of 9 planes (k-4 .. k+4), and the x/y
+// The grid is cut into work items: a TX x TY tile of (x, y) columns over a
+// block of zb planes, walked in increasing z. The paper keeps a whole z
+// column in a processing element's memory and receives x/y neighbours from 4
+// PEs per direction over the fabric (Section III-B, III-C); here the column
+// lives in a per-thread register queue of 9 planes (k-4 .. k+4), and the x/y
 // neighbours come from a shared-memory copy of plane k with its 4-cell halo.
 //
-// All three input streams arrive by TMA (cp.async.bulk.tensor) into two
-// shared-memory rings, so no register is spent on prefetching:
-//   ring A (kRingA slots): u^n tile with halo, (TX+8) x (TY+8), runs up to
-//     kRingA - 5 planes ahead of the queue;
-//   ring B (kRingB slots): u^{n-1} and (V dt/h)^2 tiles, TX x TY each, runs
-//     up to kRingB - 1 planes ahead of the plane being computed.
+// Persistent, warp-specialized CTAs (one grid of SMs x CTAs-per-SM that loops
+// over the items):
+//  - one producer lane issues every TMA copy (cp.async.bulk.tensor) into two
+//    shared-memory rings, ring A (u^n tile with halo, (TX+8) x (TY+8)) and
+//    ring B (u^{n-1} and (V dt/h)^2 tiles, TX x TY), each slot guarded by a
+//    "full" mbarrier (transaction count) and an "empty" mbarrier;
+//  - the consumer warps compute: each thread owns 4 consecutive x cells of
+//    one row, waits on "full", reads the slot, and arrives on "empty" -- no
+//    atomics, fences or divergent code in the steady state. The producer
+//    runs ahead by the ring depth, across item boundaries too.
 // u^{n+1} is written in place of u^{n-1} with 128-bit streaming stores.
 // Taper, source injection and receiver sampling are fused into the pass.
-// Each thread owns 4 consecutive x cells of one row.
-//
-// There is no CTA-wide barrier in the z loop. Every warp counts itself out of
-// a ring slot once it has read it (a shared-memory counter per slot); the
-// warp that completes the count refills the slot with the plane one ring
-// length further on. Warps drift apart by up to the ring depth instead of
-// meeting at every plane. The z loop is unrolled by 3 with the queue indices
-// rotated at compile time.
+// The z loop is unrolled by 3 with the queue indices rotated at compile time.
 //
 // Each thread's 4 cells are processed as two pairs with the packed FP32x2
 // instructions of sm_100+ (add/mul/fma .rn .f32x2), which halves the
@@ -30,6 +27,10 @@
 // scalar instruction, so the arithmetic per cell is the same expression, in
 // the same order, as the direct kernel, and the two CUDA paths agree bit for
 // bit.
+//
+// Every wait is bounded (kWaitLimitNs); on a timeout the kernel records
+// kStatusTimeout, all warps leave their loops, and the CTA waits (bounded)
+// for its copies in flight before it exits.
 #include <climits>
 
 #include "ws_internal.h"
@@ -37,10 +38,6 @@
 namespace ws {
 namespace {
 
-constexpr int kRingA = 8;   // u^n tile slots (power of two, >= 8)
-constexpr int kRingALog2 = 3;
-constexpr int kRingB = 4;   // u^{n-1} / (V dt/h)^2 slots (power of two)
-constexpr int kRingBLog2 = 2;
 constexpr int kUnroll = 3;  // planes per loop trip; divides the 9-plane queue rotation
 
 __device__ __forceinline__ unsigned smem_addr(const void *p) {
@@ -54,10 +51,6 @@ __device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
 
 __device__ __forceinline__ void fence_mbar_init() {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-__device__ __forceinline__ void fence_proxy_async_smem() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, unsigned bytes) {
@@ -136,19 +129,27 @@ __device__ __forceinline__ float2 hi2(const float4 &v) { return make_float2(v.z,
 __device__ __forceinline__ float2 pair(const float4 &v, int p) { return p == 0 ? lo2(v) : hi2(v); }
 __device__ __forceinline__ float2 splat(float x) { return make_float2(x, x); }
 
-template <int TX, int TY>
+// Arrive on an mbarrier (release semantics at CTA scope), no token kept.
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// Tile geometry and ring sizes of one streaming-kernel instantiation.
+template <int TX, int TY, int NA, int NB>
 struct StreamCfg {
-    static constexpr int kThreads = (TX / 4) * TY;
-    static constexpr int kWarps = kThreads / 32;
-    static constexpr int kRowW = TX + 2 * kHalo;   // floats per ring-A row
+    static constexpr int kConsumers = (TX / 4) * TY;   // compute threads
+    static constexpr int kThreads = kConsumers + 32;   // + one producer warp
+    static constexpr int kRowW = TX + 2 * kHalo;       // floats per ring-A row
     static constexpr int kRows = TY + 2 * kHalo;
-    static constexpr int kSlotA = kRowW * kRows;   // floats per ring-A slot
+    static constexpr int kSlotA = kRowW * kRows;       // floats per ring-A slot
     static constexpr unsigned kSlotABytes = kSlotA * 4u;
-    static constexpr int kTile = TX * TY;          // floats per field in a ring-B slot
+    static constexpr int kTile = TX * TY;              // floats per field in a ring-B slot
     static constexpr unsigned kSlotBBytes = 2u * kTile * 4u;
-    static_assert(kThreads % 32 == 0, "whole warps");
+    static_assert(kConsumers % 32 == 0, "whole consumer warps");
+    static_assert((NA & (NA - 1)) == 0 && NA >= 8, "ring A: power of two, >= 8 planes");
+    static_assert((NB & (NB - 1)) == 0 && NB >= 2, "ring B: power of two, >= 2 planes");
     static_assert(kSlotABytes % 128 == 0 && kSlotBBytes % 128 == 0, "slots stay 128-byte aligned");
-    static constexpr size_t kSmem = size_t(kRingA) * kSlotABytes + size_t(kRingB) * kSlotBBytes;
+    static constexpr size_t kSmem = size_t(NA) * kSlotABytes + size_t(NB) * kSlotBBytes;
 };
 
 // The tensor maps of one launch: u^n with the halo box, u^{n-1} and
@@ -157,145 +158,163 @@ struct StreamMaps {
     CUtensorMap u, up, w;
 };
 
-// Per-thread state of the z walk.
+// A work item: one tile of columns over one block of planes. Items are
+// numbered block-major (all tiles of block 0, then block 1, ...), so the
+// CTAs that run at the same time work on neighbouring tiles at similar
+// depths and the halo of one tile is still in L2 when its neighbour reads it.
+struct Item {
+    int i0, j0, z0, z1, tile;
+};
+
+__device__ __forceinline__ Item item_of(int item, int tiles_x, int ntiles, int zb, int nz, int TX,
+                                        int TY) {
+    Item it;
+    const int blk = item / ntiles;
+    it.tile = item - blk * ntiles;
+    const int ty = it.tile / tiles_x;
+    it.i0 = (it.tile - ty * tiles_x) * TX;
+    it.j0 = ty * TY;
+    it.z0 = blk * zb;
+    it.z1 = min(it.z0 + zb, nz);
+    return it;
+}
+
+// Shared-memory state of one CTA.
+template <int NA, int NB>
+struct Rings {
+    uint64_t fullA[NA], emptyA[NA], fullB[NB], emptyB[NB];
+    int issuedA[NA], issuedB[NB];   // copies issued into each slot (for the drain)
+    int abort;
+};
+
+// Bounded wait for a phase of an mbarrier. Gives up after kWaitLimitNs, or
+// early once another warp has aborted; returns false then.
+__device__ __forceinline__ bool wait_phase(uint64_t *bar, unsigned parity, volatile int *abort,
+                                           unsigned *status) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    unsigned n = 0;
+    while (!mbar_try_wait(bar, parity)) {
+        if ((++n & 63u) == 0) {
+            if (*abort) return false;
+            if (global_ns() - t0 > kWaitLimitNs) {
+                atomicOr(status, kStatusTimeout);
+                *abort = 1;
+                return false;
+            }
+        }
+    }
+    return true;
+}
+
+// Per-thread state of a consumer thread's walk down one item.
 struct Walk {
-    float4 q[9];            // u of planes k-4 .. k+4 (rotated: see plane_step)
+    float4 q[9];            // u^n of planes k-4 .. k+4 (rotated: see plane_step)
     float gzb[3];           // z taper of planes k, k+1, k+2 (rotated)
     float4 gxy;             // gx * gy of this thread's 4 columns
     float *out_k;           // u^{n+1} of plane k
-    long long plane;        // elements per padded plane
-    int offA;               // this thread's first cell in a ring-A row (row of plane k)
-    int offB;               // this thread's first cell in a ring-B tile
-    int z0, z1, nplanes, nvalid;
-    bool col_ok;
+    int nvalid;             // cells of the 4 inside the grid (0 when the row is outside)
     int rcur, rend, rnext_k;
     unsigned src_mask;
-    bool aborted;
+    unsigned gAw, gAr, gB;  // ring-A planes waited for / released, ring-B planes used
+    bool ok;
 };
 
-struct Rings {
-    uint64_t *fullA, *fullB;
-    int *arrivedA, *arrivedB;  // warps done with each slot, over all its uses
-    int *issuedA, *issuedB;    // copies issued into each slot
-    int *abort;
-    float *ringA, *ringB;
-};
-
-template <int TX, int TY>
+template <int TX, int TY, int NA, int NB>
 struct Kern {
-    using Cfg = StreamCfg<TX, TY>;
+    using Cfg = StreamCfg<TX, TY, NA, NB>;
+    using R = Rings<NA, NB>;
 
-    // Wait for a phase of a ring barrier; bounded, and gives up early once
-    // another warp has aborted. The outcome is made uniform across the warp.
-    static __device__ __forceinline__ void wait_bar(Walk &wk, const Rings &rg, uint64_t *bar,
-                                                    unsigned par, unsigned *status) {
-        bool fail = false;
-        if (!mbar_try_wait(bar, par)) {
-            const unsigned long long t0 = global_ns();
-            unsigned n = 0;
-            while (!mbar_try_wait(bar, par)) {
-                if ((++n & 63u) == 0) {
-                    if (*reinterpret_cast<volatile int *>(rg.abort)) {
-                        fail = true;
-                        break;
-                    }
-                    if (global_ns() - t0 > kWaitLimitNs) {
-                        atomicOr(status, kStatusTimeout);
-                        *reinterpret_cast<volatile int *>(rg.abort) = 1;
-                        fail = true;
-                        break;
-                    }
-                }
-            }
-        }
-        wk.aborted = __any_sync(0xffffffffu, fail);
-    }
+    // ---------------------------------------------------------------- producer
 
-    // Refill of ring-A slot with relative plane pr (interior plane z0-4+pr).
-    static __device__ __forceinline__ void issue_a(const Rings &rg, const StreamMaps &mp, int pr,
-                                                   int i0, int j0, int z0) {
-        const int slot = pr & (kRingA - 1);
+    // Copy relative plane pr of the item (interior plane z0 - 4 + pr, with
+    // its halo) into the g-th ring-A slot use, once its previous plane is
+    // released. The box corner is interior (i0 - 4, j0 - 4), padded
+    // (i0 + kXOff - 4, j0, z0 + pr); x is a multiple of 4 elements.
+    static __device__ __forceinline__ bool produce_a(R &rg, float *ringA, const StreamMaps &mp,
+                                                     unsigned g, const Item &it, int pr,
+                                                     unsigned *status) {
+        const int slot = g & (NA - 1);
+        if (!wait_phase(&rg.emptyA[slot], ((g / NA) & 1u) ^ 1u, &rg.abort, status)) return false;
         rg.issuedA[slot]++;
         mbar_arrive_expect_tx(&rg.fullA[slot], Cfg::kSlotABytes);
-        // box corner at interior (i0 - 4, j0 - 4, z0 - 4 + pr): padded
-        // (i0 + kXOff - 4, j0, z0 + pr); x is a multiple of 4 elements
-        tma_load_3d(rg.ringA + slot * Cfg::kSlotA, &mp.u, &rg.fullA[slot], i0 + kXOff - kHalo, j0,
-                    z0 + pr);
+        tma_load_3d(ringA + slot * Cfg::kSlotA, &mp.u, &rg.fullA[slot], it.i0 + kXOff - kHalo,
+                    it.j0, it.z0 + pr);
+        return true;
     }
 
-    // Refill of ring-B slot with plane index b (interior plane z0 + b).
-    static __device__ __forceinline__ void issue_b(const Rings &rg, const StreamMaps &mp, int b,
-                                                   int i0, int j0, int z0) {
-        const int slot = b & (kRingB - 1);
-        float *dst = rg.ringB + slot * (2 * Cfg::kTile);
+    // u^{n-1} and (V dt/h)^2 of interior plane z0 + b into the g-th ring-B use.
+    static __device__ __forceinline__ bool produce_b(R &rg, float *ringB, const StreamMaps &mp,
+                                                     unsigned g, const Item &it, int b,
+                                                     unsigned *status) {
+        const int slot = g & (NB - 1);
+        if (!wait_phase(&rg.emptyB[slot], ((g / NB) & 1u) ^ 1u, &rg.abort, status)) return false;
         rg.issuedB[slot]++;
+        float *dst = ringB + slot * (2 * Cfg::kTile);
         mbar_arrive_expect_tx(&rg.fullB[slot], Cfg::kSlotBBytes);
-        tma_load_3d(dst, &mp.up, &rg.fullB[slot], i0 + kXOff, j0 + kHalo, z0 + b + kHalo);
-        tma_load_3d(dst + Cfg::kTile, &mp.w, &rg.fullB[slot], i0 + kXOff, j0 + kHalo,
-                    z0 + b + kHalo);
+        tma_load_3d(dst, &mp.up, &rg.fullB[slot], it.i0 + kXOff, it.j0 + kHalo, it.z0 + b + kHalo);
+        tma_load_3d(dst + Cfg::kTile, &mp.w, &rg.fullB[slot], it.i0 + kXOff, it.j0 + kHalo,
+                    it.z0 + b + kHalo);
+        return true;
     }
 
-    // This warp is done reading a slot for its use-th time. True for the warp
-    // that completes the count, which then refills the slot.
-    static __device__ __forceinline__ bool last_reader(int *arrived, int slot, int use) {
-        __threadfence_block();
-        const int old = atomicAdd(&arrived[slot], 1);
-        return old == Cfg::kWarps * (use + 1) - 1;
-    }
-
-    static __device__ __forceinline__ void release_a(const Rings &rg, const StreamMaps &mp, int pr,
-                                                     int nplanes, int i0, int j0, int z0) {
-        __syncwarp();
-        if ((threadIdx.x & 31) == 0) {
-            if (last_reader(rg.arrivedA, pr & (kRingA - 1), pr >> kRingALog2) &&
-                pr + kRingA < nplanes) {
-                __threadfence_block();
-                fence_proxy_async_smem();
-                issue_a(rg, mp, pr + kRingA, i0, j0, z0);
+    // One lane issues every copy of every item of this CTA, in the order the
+    // consumers need them: the 8 planes of the queue prologue, then for each
+    // plane k of the block its u^{n-1} / (V dt/h)^2 and the u^n plane k + 8.
+    static __device__ void producer(R &rg, float *ringA, float *ringB, const StreamMaps &mp,
+                                    const StepArgs &a, int zb, int tiles_x, int ntiles,
+                                    int nitems) {
+        unsigned gA = 0, gB = 0;
+        for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
+            const Item it = item_of(item, tiles_x, ntiles, zb, a.g.nz, TX, TY);
+            const int nb = it.z1 - it.z0, nplanes = nb + 2 * kHalo;
+            for (int pr = 0; pr < 2 * kHalo; ++pr)
+                if (!produce_a(rg, ringA, mp, gA++, it, pr, a.status)) return;
+            for (int b = 0; b < nb; ++b) {
+                if (!produce_b(rg, ringB, mp, gB++, it, b, a.status)) return;
+                if (b + 2 * kHalo < nplanes &&
+                    !produce_a(rg, ringA, mp, gA++, it, b + 2 * kHalo, a.status))
+                    return;
             }
         }
     }
 
-    static __device__ __forceinline__ void release_b(const Rings &rg, const StreamMaps &mp, int b,
-                                                     int nb, int i0, int j0, int z0) {
-        __syncwarp();
-        if ((threadIdx.x & 31) == 0) {
-            if (last_reader(rg.arrivedB, b & (kRingB - 1), b >> kRingBLog2) && b + kRingB < nb) {
-                __threadfence_block();
-                fence_proxy_async_smem();
-                issue_b(rg, mp, b + kRingB, i0, j0, z0);
-            }
-        }
+    // ---------------------------------------------------------------- consumers
+
+    static __device__ __forceinline__ const float *wait_a(Walk &wk, R &rg, const float *ringA,
+                                                          unsigned g, unsigned *status) {
+        const int slot = g & (NA - 1);
+        wk.ok = wk.ok && wait_phase(&rg.fullA[slot], (g / NA) & 1u, &rg.abort, status);
+        return ringA + slot * Cfg::kSlotA;
     }
 
-    // Plane k, with the rotation R = (k - z0) mod 9 fixed at compile time.
-    template <int R>
-    static __device__ __forceinline__ void plane_step(Walk &wk, const Rings &rg,
-                                                      const StreamMaps &mp, const StepArgs &a,
-                                                      int k, int i, int j, int i0, int j0,
-                                                      const RecEntry *rec) {
-#define QI(m) ((R + (m)) % 9)
-#define BI(d) ((R + (d)) % 3)
-        const int b = k - wk.z0;        // ring-B plane index
-        const int pc = b + kHalo;       // ring-A relative index of plane k
-
+    // Plane k of the item, with the rotation R = (k - z0) mod 9 fixed at
+    // compile time.
+    template <int RQ>
+    static __device__ __forceinline__ void plane_step(Walk &wk, R &rg, const float *ringA,
+                                                      const float *ringB, const StepArgs &a,
+                                                      const Item &it, int k, int i, int j,
+                                                      int offA, int offB, const RecEntry *rec) {
+#define QI(m) ((RQ + (m)) % 9)
+#define BI(d) ((RQ + (d)) % 3)
         // u^n of plane k + 4 into the queue
-        wait_bar(wk, rg, &rg.fullA[(pc + kHalo) & (kRingA - 1)],
-                 (unsigned)((pc + kHalo) >> kRingALog2) & 1u, a.status);
-        if (wk.aborted) return;
-        wk.q[QI(8)] = lds4(rg.ringA + ((pc + kHalo) & (kRingA - 1)) * Cfg::kSlotA + wk.offA);
+        const float *sa = wait_a(wk, rg, ringA, wk.gAw, a.status);
+        wk.q[QI(8)] = lds4(sa + offA);
+        ++wk.gAw;
 
         // u^{n-1} and (V dt/h)^2 of plane k
-        wait_bar(wk, rg, &rg.fullB[b & (kRingB - 1)], (unsigned)(b >> kRingBLog2) & 1u, a.status);
-        if (wk.aborted) return;
-        const float *tb = rg.ringB + (b & (kRingB - 1)) * (2 * Cfg::kTile) + wk.offB;
+        const int sb = wk.gB & (NB - 1);
+        wk.ok = wk.ok && wait_phase(&rg.fullB[sb], (wk.gB / NB) & 1u, &rg.abort, a.status);
+        const float *tb = ringB + sb * (2 * Cfg::kTile) + offB;
         const float4 upc = lds4(tb);
         const float4 wc = lds4(tb + Cfg::kTile);
-        release_b(rg, mp, b, wk.z1 - wk.z0, i0, j0, wk.z0);
+        mbar_arrive(&rg.emptyB[sb]);
+        ++wk.gB;
 
-        if (k + 2 < wk.z1) wk.gzb[BI(2)] = __ldg(a.gz + k + 2);
+        if (k + 2 < it.z1) wk.gzb[BI(2)] = __ldg(a.gz + k + 2);
 
-        const float *row = rg.ringA + (pc & (kRingA - 1)) * Cfg::kSlotA + wk.offA;
+        // u^n of plane k with its halo (waited for four planes ago)
+        const float *row = ringA + (wk.gAr & (NA - 1)) * Cfg::kSlotA + offA;
         const float4 xl = lds4(row - 4);   // cells x-4 .. x-1 of lane 0
         const float4 xc = wk.q[QI(4)];
         const float4 xr = lds4(row + 4);   // cells x+4 .. x+7 of lane 0
@@ -305,7 +324,8 @@ struct Kern {
             yp[m - 1] = lds4(row + m * Cfg::kRowW);
             ym[m - 1] = lds4(row - m * Cfg::kRowW);
         }
-        release_a(rg, mp, pc, wk.nplanes, i0, j0, wk.z0);
+        mbar_arrive(&rg.emptyA[wk.gAr & (NA - 1)]);
+        ++wk.gAr;
 
         // x pairs: offsets +-2 and +-4 are aligned float2 pairs of (xl, xc, xr);
         // offsets +-1 and +-3 straddle pairs and are summed per lane.
@@ -358,17 +378,14 @@ struct Kern {
                 }
             }
         }
-        if (wk.col_ok) {
-            float *dst = wk.out_k;
-            if (wk.nvalid == 4) {
-                __stcs(reinterpret_cast<float4 *>(dst), out);
-            } else {
-                dst[0] = out.x;
-                if (wk.nvalid > 1) dst[1] = out.y;
-                if (wk.nvalid > 2) dst[2] = out.z;
-            }
+        if (wk.nvalid == 4) {
+            __stcs(reinterpret_cast<float4 *>(wk.out_k), out);
+        } else if (wk.nvalid > 0) {
+            wk.out_k[0] = out.x;
+            if (wk.nvalid > 1) wk.out_k[1] = out.y;
+            if (wk.nvalid > 2) wk.out_k[2] = out.z;
         }
-        wk.out_k += wk.plane;
+        wk.out_k += a.g.plane;
         if (k == wk.rnext_k) {
             while (wk.rcur < wk.rend && rec[wk.rcur].k == k) {
                 const RecEntry er = rec[wk.rcur];
@@ -392,130 +409,131 @@ struct Kern {
             for (int m = 0; m < 9; ++m) wk.q[m] = t[m];
         }
     }
+
+    static __device__ void consumer(R &rg, const float *ringA, const float *ringB, float *up,
+                                    const StepArgs &a, int zb, int tiles_x, int ntiles,
+                                    int nitems, const int *rec_ptr, const RecEntry *rec) {
+        const Geom &g = a.g;
+        const int tid = threadIdx.x;
+        const int tx = tid % (TX / 4);
+        const int ty = tid / (TX / 4);
+        const int offA = (kHalo + ty) * Cfg::kRowW + kHalo + 4 * tx;
+        const int offB = ty * TX + 4 * tx;
+        Walk wk;
+        wk.gAw = wk.gAr = wk.gB = 0;
+        wk.ok = true;
+        for (int item = blockIdx.x; item < nitems && wk.ok; item += gridDim.x) {
+            const Item it = item_of(item, tiles_x, ntiles, zb, g.nz, TX, TY);
+            const int i = it.i0 + 4 * tx;
+            const int j = it.j0 + ty;
+            const bool col_ok = (j < g.ny) && (i < g.nx);
+            wk.nvalid = col_ok ? min(4, g.nx - i) : 0;
+            wk.gxy = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (col_ok) {
+                const float gyj = a.gy[j];
+                wk.gxy.x = a.gx[i] * gyj;
+                if (wk.nvalid > 1) wk.gxy.y = a.gx[i + 1] * gyj;
+                if (wk.nvalid > 2) wk.gxy.z = a.gx[i + 2] * gyj;
+                if (wk.nvalid > 3) wk.gxy.w = a.gx[i + 3] * gyj;
+            }
+            wk.src_mask = 0u;
+            for (int qs = 0; qs < a.src.n; ++qs) {
+                const SourceSample &ss = a.src.s[qs];
+                if (ss.i >= it.i0 && ss.i < it.i0 + TX && ss.j >= it.j0 && ss.j < it.j0 + TY &&
+                    ss.k >= it.z0 && ss.k < it.z1)
+                    wk.src_mask |= 1u << qs;
+            }
+            wk.rcur = wk.rend = 0;
+            if (rec_ptr != nullptr) {
+                wk.rcur = rec_ptr[it.tile];
+                wk.rend = rec_ptr[it.tile + 1];
+                while (wk.rcur < wk.rend && rec[wk.rcur].k < it.z0) ++wk.rcur;
+            }
+            wk.rnext_k = wk.rcur < wk.rend ? rec[wk.rcur].k : INT_MAX;
+            wk.out_k = up + pidx(g, col_ok ? i : 0, col_ok ? j : 0, it.z0);
+#pragma unroll
+            for (int d = 0; d < 2; ++d)
+                wk.gzb[d] = (it.z0 + d < it.z1) ? __ldg(a.gz + it.z0 + d) : 1.0f;
+
+            // queue prologue: planes z0-4 .. z0+3; the first four are only
+            // needed here and are released at once
+#pragma unroll
+            for (int m = 0; m < 2 * kHalo; ++m) {
+                const float *sa = wait_a(wk, rg, ringA, wk.gAw, a.status);
+                wk.q[m] = lds4(sa + offA);
+                ++wk.gAw;
+            }
+#pragma unroll
+            for (int m = 0; m < kHalo; ++m) {
+                mbar_arrive(&rg.emptyA[wk.gAr & (NA - 1)]);
+                ++wk.gAr;
+            }
+            if (!wk.ok) break;
+
+            for (int kb = it.z0; kb < it.z1; kb += kUnroll) {
+#define WS_PLANE(RQ)                                                                         \
+    if (kb + (RQ) >= it.z1) break;                                                           \
+    plane_step<RQ>(wk, rg, ringA, ringB, a, it, kb + (RQ), i, j, offA, offB, rec);          \
+    if (!wk.ok) break;
+                WS_PLANE(0)
+                WS_PLANE(1)
+                WS_PLANE(2)
+#undef WS_PLANE
+                rotate_queue(wk);
+            }
+            // the last four planes (z1 .. z1+3) were needed only for the queue
+#pragma unroll
+            for (int m = 0; m < kHalo; ++m) {
+                mbar_arrive(&rg.emptyA[wk.gAr & (NA - 1)]);
+                ++wk.gAr;
+            }
+        }
+    }
 };
 
-template <int TX, int TY>
-__global__ void __launch_bounds__((TX / 4) * TY, 2)
+template <int TX, int TY, int NA, int NB, int MINB>
+__global__ void __launch_bounds__(StreamCfg<TX, TY, NA, NB>::kThreads, MINB)
     step_stream_kernel(const __grid_constant__ StreamMaps maps, float *__restrict__ up,
-                       const __grid_constant__ StepArgs a, const int zb,
-                       const int *__restrict__ rec_ptr, const RecEntry *__restrict__ rec) {
-    using K = Kern<TX, TY>;
+                       const __grid_constant__ StepArgs a, const int zb, const int tiles_x,
+                       const int ntiles, const int nitems, const int *__restrict__ rec_ptr,
+                       const RecEntry *__restrict__ rec) {
+    using K = Kern<TX, TY, NA, NB>;
     using Cfg = typename K::Cfg;
     extern __shared__ __align__(128) float smem[];
-    __shared__ __align__(8) uint64_t fullA[kRingA], fullB[kRingB];
-    __shared__ int arrivedA[kRingA], arrivedB[kRingB], issuedA[kRingA], issuedB[kRingB];
-    __shared__ int s_abort;
+    __shared__ Rings<NA, NB> rg;
+    float *ringA = smem;
+    float *ringB = smem + NA * Cfg::kSlotA;
 
-    const Geom &g = a.g;
-    const int tiles_x = (g.nx + TX - 1) / TX;
-    const int tile = blockIdx.x;
-    const int i0 = (tile % tiles_x) * TX;
-    const int j0 = (tile / tiles_x) * TY;
-    const int tid = threadIdx.x;
-    const int tx = tid % (TX / 4);
-    const int ty = tid / (TX / 4);
-    const int i = i0 + 4 * tx;
-    const int j = j0 + ty;
-
-    Walk wk;
-    wk.z0 = blockIdx.y * zb;
-    wk.z1 = min(wk.z0 + zb, g.nz);
-    wk.nplanes = (wk.z1 - wk.z0) + 2 * kHalo;  // ring-A planes: k in [z0-4, z1+4)
-    wk.col_ok = (j < g.ny) && (i < g.nx);
-    wk.nvalid = wk.col_ok ? min(4, g.nx - i) : 0;
-    wk.aborted = false;
-    const Rings rg{fullA, fullB, arrivedA, arrivedB, issuedA, issuedB, &s_abort, smem,
-                   smem + kRingA * Cfg::kSlotA};
-    const int nb = wk.z1 - wk.z0;
-
-    if (tid == 0) {
-#pragma unroll
-        for (int s = 0; s < kRingA; ++s) {
-            mbar_init(&fullA[s], 1);
-            arrivedA[s] = 0;
-            issuedA[s] = 0;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NA; ++s) {
+            mbar_init(&rg.fullA[s], 1);
+            mbar_init(&rg.emptyA[s], Cfg::kConsumers);
+            rg.issuedA[s] = 0;
         }
-#pragma unroll
-        for (int s = 0; s < kRingB; ++s) {
-            mbar_init(&fullB[s], 1);
-            arrivedB[s] = 0;
-            issuedB[s] = 0;
+        for (int s = 0; s < NB; ++s) {
+            mbar_init(&rg.fullB[s], 1);
+            mbar_init(&rg.emptyB[s], Cfg::kConsumers);
+            rg.issuedB[s] = 0;
         }
+        rg.abort = 0;
         fence_mbar_init();
-        s_abort = 0;
-        for (int pr = 0; pr < min(kRingA, wk.nplanes); ++pr) K::issue_a(rg, maps, pr, i0, j0, wk.z0);
-        for (int bb = 0; bb < min(kRingB, nb); ++bb) K::issue_b(rg, maps, bb, i0, j0, wk.z0);
     }
     __syncthreads();
 
-    wk.gxy = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (wk.col_ok) {
-        const float gyj = a.gy[j];
-        wk.gxy.x = a.gx[i] * gyj;
-        if (wk.nvalid > 1) wk.gxy.y = a.gx[i + 1] * gyj;
-        if (wk.nvalid > 2) wk.gxy.z = a.gx[i + 2] * gyj;
-        if (wk.nvalid > 3) wk.gxy.w = a.gx[i + 3] * gyj;
+    if (threadIdx.x >= Cfg::kConsumers) {
+        if (threadIdx.x == Cfg::kConsumers)
+            K::producer(rg, ringA, ringB, maps, a, zb, tiles_x, ntiles, nitems);
+    } else {
+        K::consumer(rg, ringA, ringB, up, a, zb, tiles_x, ntiles, nitems, rec_ptr, rec);
     }
 
-    // Sources inside this CTA's tile and planes.
-    wk.src_mask = 0u;
-    for (int qs = 0; qs < a.src.n; ++qs) {
-        const SourceSample &ss = a.src.s[qs];
-        if (ss.i >= i0 && ss.i < i0 + TX && ss.j >= j0 && ss.j < j0 + TY && ss.k >= wk.z0 &&
-            ss.k < wk.z1)
-            wk.src_mask |= 1u << qs;
-    }
-
-    // Receivers of this tile with k in [z0, z1), sorted by k.
-    wk.rcur = wk.rend = 0;
-    if (rec_ptr != nullptr) {
-        wk.rcur = rec_ptr[tile];
-        wk.rend = rec_ptr[tile + 1];
-        while (wk.rcur < wk.rend && rec[wk.rcur].k < wk.z0) ++wk.rcur;
-    }
-    wk.rnext_k = wk.rcur < wk.rend ? rec[wk.rcur].k : INT_MAX;
-
-    wk.offA = (kHalo + ty) * Cfg::kRowW + kHalo + 4 * tx;
-    wk.offB = ty * TX + 4 * tx;
-    wk.plane = g.plane;
-    wk.out_k = up + pidx(g, i, j, 0) + (long long)wk.z0 * g.plane;
-
-    // Prologue: queue planes z0-4 .. z0+3; z taper of planes z0, z0+1.
-#pragma unroll
-    for (int m = 0; m < 8; ++m) {
-        K::wait_bar(wk, rg, &fullA[m], 0u, a.status);
-        if (wk.aborted) break;
-        wk.q[m] = lds4(rg.ringA + m * Cfg::kSlotA + wk.offA);
-    }
-#pragma unroll
-    for (int d = 0; d < 2; ++d) wk.gzb[d] = (wk.z0 + d < wk.z1) ? __ldg(a.gz + wk.z0 + d) : 1.0f;
-
-    if (!wk.aborted) {
-        // planes z0-4 .. z0-1 were read only for the queue
-#pragma unroll
-        for (int pr = 0; pr < kHalo; ++pr) K::release_a(rg, maps, pr, wk.nplanes, i0, j0, wk.z0);
-
-        for (int kb = wk.z0; kb < wk.z1; kb += kUnroll) {
-#define WS_PLANE(R)                                                                  \
-    if (kb + (R) >= wk.z1) break;                                                    \
-    K::template plane_step<R>(wk, rg, maps, a, kb + (R), i, j, i0, j0, rec);         \
-    if (wk.aborted) break;
-            WS_PLANE(0)
-            WS_PLANE(1)
-            WS_PLANE(2)
-#undef WS_PLANE
-            K::rotate_queue(wk);
-        }
-    }
-
-    // Every warp is past the loop: no more refills. After an abort, wait
-    // (bounded) for the last copy issued into each slot to land before the
-    // CTA exits.
+    // After an abort, wait (bounded) for the last copy issued into each slot
+    // to land before the CTA exits.
     __syncthreads();
-    if (s_abort && tid == 0) {
-        for (int s = 0; s < kRingA + kRingB; ++s) {
-            const int c = s < kRingA ? issuedA[s] : issuedB[s - kRingA];
-            uint64_t *bar = s < kRingA ? &fullA[s] : &fullB[s - kRingA];
+    if (rg.abort && threadIdx.x == 0) {
+        for (int s = 0; s < NA + NB; ++s) {
+            const int c = s < NA ? rg.issuedA[s] : rg.issuedB[s - NA];
+            uint64_t *bar = s < NA ? &rg.fullA[s] : &rg.fullB[s - NA];
             if (c == 0) continue;
             const unsigned long long t0 = global_ns();
             while (!mbar_try_wait(bar, (unsigned)(c - 1) & 1u) && global_ns() - t0 < kWaitLimitNs) {
@@ -524,34 +542,38 @@ __global__ void __launch_bounds__((TX / 4) * TY, 2)
     }
 }
 
-template <int TX, int TY>
+template <int TX, int TY, int NA, int NB, int MINB>
 cudaError_t launch_tile(const StreamMaps &maps, float *up, const StepArgs &a, int zb,
                         const int *rec_ptr, const RecEntry *rec, cudaStream_t s) {
-    using Cfg = StreamCfg<TX, TY>;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(step_stream_kernel<TX, TY>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+    using Cfg = StreamCfg<TX, TY, NA, NB>;
+    auto kern = step_stream_kernel<TX, TY, NA, NB, MINB>;
+    static int ctas_per_sm = 0, sms = 0;
+    if (ctas_per_sm == 0) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)Cfg::kSmem);
         if (e != cudaSuccess) return e;
-        attr_set = true;
+        int dev = 0;
+        e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas_per_sm, kern, Cfg::kThreads,
+                                                              Cfg::kSmem);
+        if (e != cudaSuccess) return e;
+        if (ctas_per_sm < 1) return cudaErrorInvalidConfiguration;
     }
-    const int tiles = ((a.g.nx + TX - 1) / TX) * ((a.g.ny + TY - 1) / TY);
-    const int chunks = (a.g.nz + zb - 1) / zb;
-    dim3 grid(tiles, chunks, 1);
-    step_stream_kernel<TX, TY><<<grid, Cfg::kThreads, Cfg::kSmem, s>>>(maps, up, a, zb, rec_ptr, rec);
+    const int tiles_x = (a.g.nx + TX - 1) / TX;
+    const int ntiles = tiles_x * ((a.g.ny + TY - 1) / TY);
+    const int nitems = ntiles * ((a.g.nz + zb - 1) / zb);
+    const int grid = min(nitems, sms * ctas_per_sm);
+    kern<<<grid, Cfg::kThreads, Cfg::kSmem, s>>>(maps, up, a, zb, tiles_x, ntiles, nitems, rec_ptr,
+                                                 rec);
     return cudaGetLastError();
 }
 
 }  // namespace
 
 bool stream_tiling_supported(int tx, int ty) {
-    return (tx == 32 || tx == 64) && (ty == 8 || ty == 16);
-}
-
-size_t stream_smem_bytes(const StreamTiling &t) {
-    return size_t(kRingA) * size_t(t.tx + 2 * kHalo) * size_t(t.ty + 2 * kHalo) * 4u +
-           size_t(kRingB) * 2u * size_t(t.tx) * size_t(t.ty) * 4u;
+    return (tx == 64 && (ty == 8 || ty == 16 || ty == 32)) || (tx == 32 && (ty == 8 || ty == 16));
 }
 
 cudaError_t launch_step_stream(const CUtensorMap *tmap_u, const CUtensorMap *tmap_up,
@@ -562,10 +584,12 @@ cudaError_t launch_step_stream(const CUtensorMap *tmap_u, const CUtensorMap *tma
     maps.u = *tmap_u;
     maps.up = *tmap_up;
     maps.w = *tmap_w;
-    if (t.tx == 64 && t.ty == 16) return launch_tile<64, 16>(maps, up, a, t.zb, rec_ptr, rec, s);
-    if (t.tx == 64 && t.ty == 8) return launch_tile<64, 8>(maps, up, a, t.zb, rec_ptr, rec, s);
-    if (t.tx == 32 && t.ty == 16) return launch_tile<32, 16>(maps, up, a, t.zb, rec_ptr, rec, s);
-    if (t.tx == 32 && t.ty == 8) return launch_tile<32, 8>(maps, up, a, t.zb, rec_ptr, rec, s);
+    // ring sizes chosen so that the CTAs of one SM fit in its shared memory
+    if (t.tx == 64 && t.ty == 32) return launch_tile<64, 32, 8, 4, 1>(maps, up, a, t.zb, rec_ptr, rec, s);
+    if (t.tx == 64 && t.ty == 16) return launch_tile<64, 16, 8, 4, 2>(maps, up, a, t.zb, rec_ptr, rec, s);
+    if (t.tx == 64 && t.ty == 8) return launch_tile<64, 8, 8, 4, 3>(maps, up, a, t.zb, rec_ptr, rec, s);
+    if (t.tx == 32 && t.ty == 16) return launch_tile<32, 16, 8, 4, 3>(maps, up, a, t.zb, rec_ptr, rec, s);
+    if (t.tx == 32 && t.ty == 8) return launch_tile<32, 8, 8, 4, 4>(maps, up, a, t.zb, rec_ptr, rec, s);
     return cudaErrorInvalidValue;
 }
 
