@@ -108,7 +108,7 @@ struct ws_handle {
     int rec_tiling_tx = 0, rec_tiling_ty = 0;
 
     int kernel = WS_KERNEL_AUTO;
-    ws::StreamTiling tiling{32, 16, 0};
+    ws::StreamTiling tiling{64, 8, 0};
     CUtensorMap tmap_halo[2];  // buf[b] with the (tx+8, ty+8, 1) box
     CUtensorMap tmap_tile[2];  // buf[b] with the (tx, ty, 1) box
     CUtensorMap tmap_w;        // w with the (tx, ty, 1) box
@@ -163,7 +163,7 @@ int pick_kernel(ws_t ws, ws::StreamTiling *tiling) {
     if (ws->kernel == WS_KERNEL_DIRECT) return WS_KERNEL_DIRECT;
     ws::StreamTiling t = ws->tiling;
     if (ws->kernel == WS_KERNEL_AUTO && !stream_fits(ws, t)) {
-        const ws::StreamTiling cands[3] = {{64, 8, 0}, {32, 8, 0}, {64, 16, 0}};
+        const ws::StreamTiling cands[3] = {{32, 16, 0}, {32, 8, 0}, {64, 16, 0}};
         bool found = false;
         for (const auto &c : cands)
             if (stream_fits(ws, c)) {

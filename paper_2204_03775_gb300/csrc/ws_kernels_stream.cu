@@ -38,7 +38,14 @@
 namespace ws {
 namespace {
 
-constexpr int kUnroll = 3;  // planes per loop trip; divides the 9-plane queue rotation
+#ifndef WS_STREAM_UNROLL
+#define WS_STREAM_UNROLL 3
+#endif
+constexpr int kUnroll = WS_STREAM_UNROLL;  // planes per loop trip: 3 or 9 (divides the queue rotation)
+static_assert(kUnroll == 3 || kUnroll == 9, "the 9-plane queue rotation needs 3 or 9");
+#ifndef WS_RING_A
+#define WS_RING_A 8
+#endif
 
 __device__ __forceinline__ unsigned smem_addr(const void *p) {
     return static_cast<unsigned>(__cvta_generic_to_shared(p));
@@ -86,8 +93,16 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, u
         : "memory");
 }
 
+// 128-bit shared-memory load, kept whole: a warp reading 16-byte cells at
+// 16-byte stride is conflict-free only as one 128-bit access per thread (two
+// 64-bit halves would each hit every bank twice). Volatile, so it stays after
+// the barrier wait that guards the data.
 __device__ __forceinline__ float4 lds4(const float *p) {
-    return *reinterpret_cast<const float4 *>(p);
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "r"(smem_addr(p)));
+    return v;
 }
 
 __device__ __forceinline__ float comp(const float4 &v, int l) {
@@ -129,9 +144,17 @@ __device__ __forceinline__ float2 hi2(const float4 &v) { return make_float2(v.z,
 __device__ __forceinline__ float2 pair(const float4 &v, int p) { return p == 0 ? lo2(v) : hi2(v); }
 __device__ __forceinline__ float2 splat(float x) { return make_float2(x, x); }
 
-// Arrive on an mbarrier (release semantics at CTA scope), no token kept.
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+// A warp is done with a ring slot: after __syncwarp orders every lane's
+// reads, lane 0 alone arrives (release semantics at CTA scope) on the slot's
+// "empty" barrier, whose expected count is the number of consumer warps.
+__device__ __forceinline__ void warp_arrive(uint64_t *bar) {
+    __syncwarp();
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t.reg .u32 l;\n\t"
+        "mov.u32 l, %%laneid;\n\t"
+        "setp.eq.u32 p, l, 0;\n\t"
+        "@p mbarrier.arrive.shared::cta.b64 _, [%0];\n\t}" ::"r"(smem_addr(bar))
+        : "memory");
 }
 
 // Tile geometry and ring sizes of one streaming-kernel instantiation.
@@ -308,7 +331,7 @@ struct Kern {
         const float *tb = ringB + sb * (2 * Cfg::kTile) + offB;
         const float4 upc = lds4(tb);
         const float4 wc = lds4(tb + Cfg::kTile);
-        mbar_arrive(&rg.emptyB[sb]);
+        warp_arrive(&rg.emptyB[sb]);
         ++wk.gB;
 
         if (k + 2 < it.z1) wk.gzb[BI(2)] = __ldg(a.gz + k + 2);
@@ -324,7 +347,7 @@ struct Kern {
             yp[m - 1] = lds4(row + m * Cfg::kRowW);
             ym[m - 1] = lds4(row - m * Cfg::kRowW);
         }
-        mbar_arrive(&rg.emptyA[wk.gAr & (NA - 1)]);
+        warp_arrive(&rg.emptyA[wk.gAr & (NA - 1)]);
         ++wk.gAr;
 
         // x pairs: offsets +-2 and +-4 are aligned float2 pairs of (xl, xc, xr);
@@ -465,7 +488,7 @@ struct Kern {
             }
 #pragma unroll
             for (int m = 0; m < kHalo; ++m) {
-                mbar_arrive(&rg.emptyA[wk.gAr & (NA - 1)]);
+                warp_arrive(&rg.emptyA[wk.gAr & (NA - 1)]);
                 ++wk.gAr;
             }
             if (!wk.ok) break;
@@ -478,13 +501,21 @@ struct Kern {
                 WS_PLANE(0)
                 WS_PLANE(1)
                 WS_PLANE(2)
+                if constexpr (kUnroll == 9) {
+                    WS_PLANE(3)
+                    WS_PLANE(4)
+                    WS_PLANE(5)
+                    WS_PLANE(6)
+                    WS_PLANE(7)
+                    WS_PLANE(8)
+                }
 #undef WS_PLANE
                 rotate_queue(wk);
             }
             // the last four planes (z1 .. z1+3) were needed only for the queue
 #pragma unroll
             for (int m = 0; m < kHalo; ++m) {
-                mbar_arrive(&rg.emptyA[wk.gAr & (NA - 1)]);
+                warp_arrive(&rg.emptyA[wk.gAr & (NA - 1)]);
                 ++wk.gAr;
             }
         }
@@ -507,12 +538,12 @@ __global__ void __launch_bounds__(StreamCfg<TX, TY, NA, NB>::kThreads, MINB)
     if (threadIdx.x == 0) {
         for (int s = 0; s < NA; ++s) {
             mbar_init(&rg.fullA[s], 1);
-            mbar_init(&rg.emptyA[s], Cfg::kConsumers);
+            mbar_init(&rg.emptyA[s], Cfg::kConsumers / 32);
             rg.issuedA[s] = 0;
         }
         for (int s = 0; s < NB; ++s) {
             mbar_init(&rg.fullB[s], 1);
-            mbar_init(&rg.emptyB[s], Cfg::kConsumers);
+            mbar_init(&rg.emptyB[s], Cfg::kConsumers / 32);
             rg.issuedB[s] = 0;
         }
         rg.abort = 0;
@@ -588,7 +619,8 @@ cudaError_t launch_step_stream(const CUtensorMap *tmap_u, const CUtensorMap *tma
     if (t.tx == 64 && t.ty == 32) return launch_tile<64, 32, 8, 4, 1>(maps, up, a, t.zb, rec_ptr, rec, s);
     if (t.tx == 64 && t.ty == 16) return launch_tile<64, 16, 8, 4, 2>(maps, up, a, t.zb, rec_ptr, rec, s);
     if (t.tx == 64 && t.ty == 8) return launch_tile<64, 8, 8, 4, 3>(maps, up, a, t.zb, rec_ptr, rec, s);
-    if (t.tx == 32 && t.ty == 16) return launch_tile<32, 16, 8, 4, 3>(maps, up, a, t.zb, rec_ptr, rec, s);
+    if (t.tx == 32 && t.ty == 16)
+        return launch_tile<32, 16, WS_RING_A, 4, 3>(maps, up, a, t.zb, rec_ptr, rec, s);
     if (t.tx == 32 && t.ty == 8) return launch_tile<32, 8, 8, 4, 4>(maps, up, a, t.zb, rec_ptr, rec, s);
     return cudaErrorInvalidValue;
 }
