@@ -131,6 +131,15 @@ int ws_write_field(ws_t ws, const float *u, const float *u_prev, long long step,
 /* Number of steps taken since creation (or the last ws_write_field). */
 int ws_get_step(ws_t ws, long long *step);
 
+/* Discrete energy of the current state, in double precision:
+ *     E = sum (u^n - u^{n-1})^2 / (V dt)^2 - sum u^n (Lap u^{n-1})
+ * over the interior, Lap the 25-point Laplacian with the zero halo. Without
+ * sources and damping the leapfrog recurrence of Eq. 2 conserves E exactly
+ * (in exact arithmetic), since Lap is symmetric. Deterministic (fixed-order
+ * reduction over per-block partial sums in memory the handle owns).
+ * Synchronizes the stream. Errors: STATE (no velocity model), CUDA. */
+int ws_energy(ws_t ws, double *e);
+
 /* Choose the step kernel (WS_KERNEL_*) and, for WS_KERNEL_STREAM, its tile:
  * tile_x x tile_y in {32x8, 32x16, 64x8, 64x16, 64x32} (0, 0 = keep the
  * current tile; the default is 64x8), zblock >= 1 planes per work item

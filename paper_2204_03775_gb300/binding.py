@@ -74,6 +74,7 @@ def load_library(build_if_missing: bool = False):
         "ws_set_kernel": (i, [vp, i, i, i, i]),
         "ws_synchronize": (i, [vp]),
         "ws_launch_count": (ll, [vp]),
+        "ws_energy": (i, [vp, ctypes.POINTER(d)]),
         "ws_last_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -222,6 +223,12 @@ def ws_set_kernel(ws: Handle, kernel: int, tile_x: int = 0, tile_y: int = 0, zbl
 
 def ws_synchronize(ws: Handle) -> None:
     _check(load_library().ws_synchronize(ws.ptr), "ws_synchronize")
+
+
+def ws_energy(ws: Handle) -> float:
+    e = ctypes.c_double()
+    _check(load_library().ws_energy(ws.ptr, ctypes.byref(e)), "ws_energy")
+    return e.value
 
 
 def ws_launch_count(ws: Handle) -> int:

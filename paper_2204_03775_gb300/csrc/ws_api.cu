@@ -91,6 +91,7 @@ struct ws_handle {
     float *w = nullptr;                  // (V dt / h)^2, padded
     float *gx = nullptr, *gy = nullptr, *gz = nullptr;
     unsigned *status = nullptr;          // [0] status bits, [1] vmax bits, [2] vmin bits
+    double *energy = nullptr;            // energy partial sums, then the total
     cudaStream_t stream = nullptr;
     bool vel_ok = false;
     int nb = 0;
@@ -286,6 +287,7 @@ void destroy(ws_t ws) {
     cudaFree(ws->gy);
     cudaFree(ws->gz);
     cudaFree(ws->status);
+    cudaFree(ws->energy);
     free_receivers(ws);
     delete ws;
 }
@@ -324,6 +326,8 @@ int ws_create(ws_t *out, int nx, int ny, int nz, double h, double dt) {
     if (e == cudaSuccess) e = cudaMalloc(&ws->gy, sizeof(float) * ny);
     if (e == cudaSuccess) e = cudaMalloc(&ws->gz, sizeof(float) * nz);
     if (e == cudaSuccess) e = cudaMalloc(&ws->status, sizeof(unsigned) * 4);
+    if (e == cudaSuccess)
+        e = cudaMalloc(&ws->energy, sizeof(double) * (ws::energy_partial_count(ny, nz) + 1));
     for (int b = 0; b < 2 && e == cudaSuccess; ++b) e = cudaMemsetAsync(ws->buf[b], 0, fb, ws->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ws->w, 0, fb, ws->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ws->status, 0, sizeof(unsigned) * 4, ws->stream);
@@ -593,6 +597,21 @@ int ws_synchronize(ws_t ws) {
         WS_CUDA(cudaMemset(ws->status, 0, sizeof(unsigned)), "ws_synchronize");
         return fail(WS_ERR_TIMEOUT, "a bounded device wait ran out in a step kernel");
     }
+    return WS_OK;
+}
+
+int ws_energy(ws_t ws, double *e) {
+    if (!ws || !e) return fail(WS_ERR_BADARG, "ws_energy: NULL argument");
+    if (!ws->vel_ok) return fail(WS_ERR_STATE, "ws_energy: no valid velocity model");
+    const ws::Coeffs64 c{kW0, kW1, kW2, kW3, kW4};
+    const long long np = ws::energy_partial_count(ws->g.ny, ws->g.nz);
+    WS_CUDA(ws::launch_energy_padded(ws->buf[ws->cur], ws->buf[1 - ws->cur], ws->w, ws->g, ws->h, c,
+                                     ws->energy, ws->energy + np, ws->stream),
+            "energy kernels");
+    ws->launches += 2;
+    WS_CUDA(cudaMemcpyAsync(e, ws->energy + np, sizeof(double), cudaMemcpyDeviceToHost, ws->stream),
+            "ws_energy");
+    WS_CUDA(cudaStreamSynchronize(ws->stream), "ws_energy");
     return WS_OK;
 }
 

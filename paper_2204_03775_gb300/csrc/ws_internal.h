@@ -25,6 +25,11 @@ struct Coeffs {
     float c0x3, c1, c2, c3, c4;
 };
 
+// The same weights in double precision, centre weight for one axis.
+struct Coeffs64 {
+    double c0, c1, c2, c3, c4;
+};
+
 // Per-launch source samples: cell and (h^2 * s(t_n)); the kernel multiplies
 // by the stored (V dt / h)^2 of the cell, which gives (V dt)^2 s(t_n).
 struct SourceSample {
@@ -104,5 +109,13 @@ cudaError_t launch_step_stream(const CUtensorMap *tmap_u, const CUtensorMap *tma
                                const CUtensorMap *tmap_w, float *up, const StepArgs &a,
                                const StreamTiling &t, const int *rec_ptr, const RecEntry *rec,
                                cudaStream_t s);
+
+// Discrete energy (FP64): partial sums per (row block, plane) into
+// partials[energy_partial_count(ny, nz)], then their fixed-order sum into *out.
+int energy_rows_per_block();
+long long energy_partial_count(int ny, int nz);
+cudaError_t launch_energy_padded(const float *u, const float *p, const float *w, const Geom &g,
+                                 double h, const Coeffs64 &c, double *partials, double *out,
+                                 cudaStream_t s);
 
 }  // namespace ws
