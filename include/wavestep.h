@@ -140,6 +140,35 @@ int ws_get_step(ws_t ws, long long *step);
  * Synchronizes the stream. Errors: STATE (no velocity model), CUDA. */
 int ws_energy(ws_t ws, double *e);
 
+/* The energy of ws_energy for device arrays the caller
+ * owns, without allocating any device memory. The paper has no counterpart;
+ * this entry point exists for callers that cannot call cudaMalloc: code that
+ * runs under an allocator which forbids it or has no memory to spare, and
+ * code that must not risk the implicit device-wide synchronization that
+ * cudaMalloc may perform.
+ *
+ * u, u_prev, v: device pointers to unpadded [nz][ny][nx] float32 arrays of
+ * u^n, u^{n-1} and the velocity (m/s, finite and > 0; not checked); h, dt as
+ * in ws_create. e: device pointer to one double, which receives E. Work is
+ * issued on cuda_stream (NULL = legacy default stream) and the call returns
+ * without waiting for it. E equals what ws_energy returns for a handle in
+ * that state (same per-cell terms and summation order).
+ *
+ * Scratch: the per-block partial sums live in a static device array of
+ * WS_NOALLOC_MAX_PARTIALS doubles (256 KiB) that every GPU which loads the
+ * library holds until the process exits. A grid needs ceil(ny / 32) * nz
+ * partial sums (1024 x 1024 x 1024 fits exactly); larger grids are rejected
+ * with BADARG. Every call shares that array and leaves its partial sums
+ * there; each call writes every partial it later reads, so nothing needs to
+ * start at zero, but calls whose work overlaps on the GPU (other streams,
+ * other host threads) race and give wrong results: serialize them.
+ * The first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.
+ * Errors: BADARG, CUDA. */
+#define WS_NOALLOC_MAX_PARTIALS 32768
+int ws_energy_noalloc(const float *u, const float *u_prev, const float *v, int nx, int ny, int nz,
+                      double h, double dt, double *e, void *cuda_stream);
+
 /* Choose the step kernel (WS_KERNEL_*) and, for WS_KERNEL_STREAM, its tile:
  * tile_x x tile_y in {32x8, 32x16, 64x8, 64x16, 64x32} (0, 0 = keep the
  * current tile; the default is 64x8), zblock >= 1 planes per work item

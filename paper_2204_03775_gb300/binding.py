@@ -75,6 +75,7 @@ def load_library(build_if_missing: bool = False):
         "ws_synchronize": (i, [vp]),
         "ws_launch_count": (ll, [vp]),
         "ws_energy": (i, [vp, ctypes.POINTER(d)]),
+        "ws_energy_noalloc": (i, [vp, vp, vp, i, i, i, d, d, vp, vp]),
         "ws_last_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -229,6 +230,23 @@ def ws_energy(ws: Handle) -> float:
     e = ctypes.c_double()
     _check(load_library().ws_energy(ws.ptr, ctypes.byref(e)), "ws_energy")
     return e.value
+
+
+def ws_energy_noalloc(u, u_prev, v, h: float, dt: float, out, stream=None) -> None:
+    """Energy of device arrays [nz][ny][nx] into the device double out[0]; allocates nothing."""
+    import torch
+    for t in (u, u_prev, v):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32
+                and t.is_contiguous() and t.dim() == 3 and t.shape == u.shape):
+            raise TypeError("u, u_prev, v: contiguous float32 CUDA tensors of one [nz][ny][nx] shape")
+    if not (isinstance(out, torch.Tensor) and out.is_cuda and out.dtype == torch.float64):
+        raise TypeError("out: a float64 CUDA tensor")
+    nz, ny, nx = u.shape
+    raw = getattr(stream, "cuda_stream", stream)
+    _check(load_library().ws_energy_noalloc(
+        ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(u_prev.data_ptr()),
+        ctypes.c_void_p(v.data_ptr()), nx, ny, nz, float(h), float(dt),
+        ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(raw or None)), "ws_energy_noalloc")
 
 
 def ws_launch_count(ws: Handle) -> int:

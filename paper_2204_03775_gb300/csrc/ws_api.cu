@@ -615,6 +615,27 @@ int ws_energy(ws_t ws, double *e) {
     return WS_OK;
 }
 
+int ws_energy_noalloc(const float *u, const float *u_prev, const float *v, int nx, int ny, int nz,
+                      double h, double dt, double *e, void *cuda_stream) {
+    if (!u || !u_prev || !v || !e) return fail(WS_ERR_BADARG, "ws_energy_noalloc: NULL argument");
+    if (nx < 1 || ny < 1 || nz < 1 || nx > 65535 || ny > 65535 || nz > 65535)
+        return fail(WS_ERR_BADARG, "ws_energy_noalloc: sizes must be in [1, 65535], got %d x %d x %d",
+                    nx, ny, nz);
+    if (!(h > 0.0) || !(dt > 0.0) || !std::isfinite(h) || !std::isfinite(dt))
+        return fail(WS_ERR_BADARG, "ws_energy_noalloc: h and dt must be finite and > 0");
+    const long long np = ws::energy_partial_count(ny, nz);
+    if (np > ws::kNoAllocMaxPartials)
+        return fail(WS_ERR_BADARG,
+                    "ws_energy_noalloc: %d x %d x %d needs %lld partial sums, ceil(ny/%d)*nz, but "
+                    "the static scratch holds %d",
+                    nx, ny, nz, np, ws::energy_rows_per_block(), ws::kNoAllocMaxPartials);
+    const ws::Coeffs64 c{kW0, kW1, kW2, kW3, kW4};
+    WS_CUDA(ws::launch_energy_noalloc(u, u_prev, v, nx, ny, nz, h, dt, c, e,
+                                      static_cast<cudaStream_t>(cuda_stream)),
+            "ws_energy_noalloc");
+    return WS_OK;
+}
+
 long long ws_launch_count(ws_t ws) { return ws ? ws->launches : -1; }
 
 }  // extern "C"

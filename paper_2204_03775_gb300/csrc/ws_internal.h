@@ -118,4 +118,13 @@ cudaError_t launch_energy_padded(const float *u, const float *p, const float *w,
                                  double h, const Coeffs64 &c, double *partials, double *out,
                                  cudaStream_t s);
 
+// The same reduction over unpadded caller arrays, with the partial sums in a
+// static device array instead of allocated memory (at most
+// kNoAllocMaxPartials of them). out is a device pointer.
+constexpr int kNoAllocMaxPartials = WS_NOALLOC_MAX_PARTIALS;
+constexpr int kNoAllocMaxDevices = 64;
+cudaError_t launch_energy_noalloc(const float *u, const float *p, const float *v, int nx, int ny,
+                                  int nz, double h, double dt, const Coeffs64 &c, double *out,
+                                  cudaStream_t s);
+
 }  // namespace ws

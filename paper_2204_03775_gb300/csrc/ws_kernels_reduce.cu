@@ -9,12 +9,18 @@
 // the float fields: each block sums a fixed set of rows into one partial,
 // and one block adds the partials in a fixed order, so the result does not
 // depend on scheduling.
+#include <mutex>
+
 #include "ws_internal.h"
 
 namespace ws {
 namespace {
 
 constexpr int kThreads = 256;
+
+// Scratch of the allocation-free entry point: the per-block partial sums,
+// one array per device that loads the library, held until the process exits.
+static __device__ __align__(256) double g_noalloc_partials[kNoAllocMaxPartials];
 
 // u^n / u^{n-1} / (V dt / h)^2 of the handle's padded layout (halo is zero).
 struct PaddedFields {
@@ -23,6 +29,26 @@ struct PaddedFields {
     __device__ float u_at(int i, int j, int k) const { return u[pidx(g, i, j, k)]; }
     __device__ float p_at(int i, int j, int k) const { return p[pidx(g, i, j, k)]; }
     __device__ float w_at(int i, int j, int k) const { return w[pidx(g, i, j, k)]; }
+};
+
+// Unpadded [nz][ny][nx] caller arrays; (V dt / h)^2 is formed from the
+// velocity exactly as the stepper stores it (double, rounded once to float),
+// and cells outside the grid read as zero, so every cell's term is the one
+// the padded variant computes.
+struct DenseFields {
+    const float *u, *p, *v;
+    int nx, ny, nz;
+    double dt_over_h;
+    __device__ long long at(int i, int j, int k) const { return ((long long)k * ny + j) * nx + i; }
+    __device__ float u_at(int i, int j, int k) const { return u[at(i, j, k)]; }
+    __device__ float p_at(int i, int j, int k) const {
+        const bool in = i >= 0 && i < nx && j >= 0 && j < ny && k >= 0 && k < nz;
+        return in ? p[at(i, j, k)] : 0.0f;
+    }
+    __device__ float w_at(int i, int j, int k) const {
+        const double r = (double)v[at(i, j, k)] * dt_over_h;
+        return (float)(r * r);
+    }
 };
 
 // Block (x = row block jb, y = plane k) sums rows [jb*rows, jb*rows+rows) of
@@ -111,6 +137,33 @@ cudaError_t launch_energy_padded(const float *u, const float *p, const float *w,
                                  cudaStream_t s) {
     PaddedFields f{u, p, w, g};
     return launch_energy(f, g.nx, g.ny, g.nz, h, c, partials, out, s);
+}
+
+cudaError_t launch_energy_noalloc(const float *u, const float *p, const float *v, int nx, int ny,
+                                  int nz, double h, double dt, const Coeffs64 &c, double *out,
+                                  cudaStream_t s) {
+    // Host code cannot pass g_noalloc_partials itself (in host code the name
+    // is a stand-in, not a device address): look its address up once per
+    // device, with that device current.
+    static std::mutex mu;
+    static double *addr[kNoAllocMaxDevices] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return cudaErrorInvalidDevice;
+    double *partials;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (addr[dev] == nullptr) {
+            void *ptr = nullptr;
+            e = cudaGetSymbolAddress(&ptr, g_noalloc_partials);
+            if (e != cudaSuccess) return e;
+            addr[dev] = static_cast<double *>(ptr);
+        }
+        partials = addr[dev];
+    }
+    DenseFields f{u, p, v, nx, ny, nz, dt / h};
+    return launch_energy(f, nx, ny, nz, h, c, partials, out, s);
 }
 
 }  // namespace ws
