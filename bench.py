@@ -159,7 +159,7 @@ def cpu_baseline(w, target_s=15.0):
     oracle.run(w.vel[:4], w.h, w.dt, 2, sponge=w.sponge, window=(0, 0, 0, w.nx, w.ny, w.nz))
     rate = 2 * 4 * w.nx * w.ny / (time.perf_counter() - t0)
     depth = int(min(w.nz, max(w.sources[0][2] + 5, 32)))
-    steps = int(max(2, min(40, target_s * rate / (depth * w.nx * w.ny))))
+    steps = int(max(2, min(400, target_s * rate / (depth * w.nx * w.ny))))
     slab = np.ascontiguousarray(w.vel[:depth])
     t0 = time.perf_counter()
     oracle.run(slab, w.h, w.dt, steps, sources=w.sources, receivers=None, sponge=w.sponge,
