@@ -9,7 +9,10 @@
  * with Lap the 25-point, 8th-order star Laplacian of Section II (four
  * neighbours per side on each axis; weights c_0..c_4 = -205/72, 8/5, -1/5,
  * 8/315, -1/560 divided by h^2, the centre weight applied once per axis as in
- * Section III-C-2), in the time loop of Algorithm 1 starting from
+ * Section III-C-2; evaluated as sum_m c_m (s_m - 6u), s_m the sum of the six
+ * neighbours at distance m, which equals it in exact arithmetic and keeps the
+ * float operator exactly zero on constant fields), in the time loop of
+ * Algorithm 1 starting from
  * u^{-1} = u^0 = 0. Each step is one fused pass on the GPU that also applies
  * an absorbing taper, injects Ricker sources and records receivers; the paper
  * leaves boundary conditions and I/O unevaluated (Section II), so those three
@@ -54,6 +57,11 @@ extern "C" {
 #define WS_KERNEL_AUTO    0  /* the streaming kernel when the grid fits its tile, else DIRECT */
 #define WS_KERNEL_DIRECT  1  /* one thread per cell, neighbours loaded from global memory */
 #define WS_KERNEL_STREAM  2  /* z-streaming: TMA rings + 9-plane register queue, persistent */
+
+/* Storage of the two wavefield levels (ws_set_storage). */
+#define WS_STORAGE_FP32   0  /* float32 fields and model: 16 bytes per cell update */
+#define WS_STORAGE_BF16   1  /* bfloat16 fields, float32 model: 10 bytes per cell update */
+#define WS_STORAGE_FP16   2  /* float16 fields, float32 model: 10 bytes per cell update */
 
 #define WS_MAX_SOURCES   16
 
@@ -168,6 +176,19 @@ int ws_energy(ws_t ws, double *e);
 #define WS_NOALLOC_MAX_PARTIALS 32768
 int ws_energy_noalloc(const float *u, const float *u_prev, const float *v, int nx, int ny, int nz,
                       double h, double dt, double *e, void *cuda_stream);
+
+/* Store u^n and u^{n-1} in 16 bits (WS_STORAGE_BF16 or WS_STORAGE_FP16;
+ * (V dt/h)^2 stays FP32: 10 bytes per cell update instead of 16) or back in
+ * FP32. Arithmetic stays FP32. Each stored field carries its own power-of-two
+ * scale: the step that writes u^{n+1} picks it on the device from max|u^n|
+ * and the source amplitude, placing the field's maximum near 2^12 (16x under
+ * the FP16 limit). The current state is converted (rounded once). 16-bit
+ * storage runs the streaming kernel with a 64x8 tile and needs nx >= 64,
+ * ny >= 8, else BADARG. ws_read_field, ws_write_field and ws_energy
+ * convert to and from FP32 (ws_energy then uses the FP32 model). This
+ * realizes the reduced-precision storage that the paper contrasts with its
+ * FP32-only arithmetic (Section I). */
+int ws_set_storage(ws_t ws, int storage);
 
 /* Choose the step kernel (WS_KERNEL_*) and, for WS_KERNEL_STREAM, its tile:
  * tile_x x tile_y in {32x8, 32x16, 64x8, 64x16, 64x32} (0, 0 = keep the

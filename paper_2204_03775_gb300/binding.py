@@ -28,6 +28,10 @@ WS_KERNEL_AUTO = 0
 WS_KERNEL_DIRECT = 1
 WS_KERNEL_STREAM = 2
 
+WS_STORAGE_FP32 = 0
+WS_STORAGE_BF16 = 1
+WS_STORAGE_FP16 = 2
+
 WS_MAX_SOURCES = 16
 
 
@@ -72,6 +76,7 @@ def load_library(build_if_missing: bool = False):
         "ws_write_field": (i, [vp, vp, vp, ll, i]),
         "ws_get_step": (i, [vp, ctypes.POINTER(ll)]),
         "ws_set_kernel": (i, [vp, i, i, i, i]),
+        "ws_set_storage": (i, [vp, i]),
         "ws_synchronize": (i, [vp]),
         "ws_launch_count": (ll, [vp]),
         "ws_energy": (i, [vp, ctypes.POINTER(d)]),
@@ -220,6 +225,10 @@ def ws_get_step(ws: Handle) -> int:
 def ws_set_kernel(ws: Handle, kernel: int, tile_x: int = 0, tile_y: int = 0, zblock: int = 0) -> None:
     _check(load_library().ws_set_kernel(ws.ptr, int(kernel), int(tile_x), int(tile_y), int(zblock)),
            "ws_set_kernel")
+
+
+def ws_set_storage(ws: Handle, storage: int) -> None:
+    _check(load_library().ws_set_storage(ws.ptr, int(storage)), "ws_set_storage")
 
 
 def ws_synchronize(ws: Handle) -> None:

@@ -115,6 +115,14 @@ struct ws_handle {
     CUtensorMap tmap_w;        // w with the (tx, ty, 1) box
     bool tmap_ok = false;
     long long launches = 0;
+
+    // 16-bit storage (WS_STORAGE_BF16 / WS_STORAGE_FP16): the wavefields live
+    // in buf16 (buf then serves as FP32 scratch copies); the model stays in w.
+    int storage = WS_STORAGE_FP32;
+    uint16_t *buf16[2] = {nullptr, nullptr};
+    ws::Scale16 *scale = nullptr;
+    CUtensorMap t16_halo[2], t16_tile[2], t16_w;  // t16_w: FP32 model, 16-bit tile box
+    double wmax = 0.0;         // max (V dt / h)^2 of the model
 };
 
 namespace {
@@ -123,14 +131,17 @@ size_t field_bytes(const ws::Geom &g) {
     return size_t(g.pnx) * size_t(g.pny) * size_t(g.pnz) * sizeof(float);
 }
 
-int encode_map(CUtensorMap *map, void *base, const ws::Geom &g, int bx, int by) {
+int encode_map(CUtensorMap *map, void *base, const ws::Geom &g, int bx, int by,
+               int elem_bytes = 4) {
     PFN_cuTensorMapEncodeTiled_v12000 enc = get_encode_fn();
     if (!enc) return fail(WS_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
     cuuint64_t dims[3] = {(cuuint64_t)g.pnx, (cuuint64_t)g.pny, (cuuint64_t)g.pnz};
-    cuuint64_t strides[2] = {(cuuint64_t)g.pnx * 4, (cuuint64_t)g.plane * 4};
+    cuuint64_t strides[2] = {(cuuint64_t)g.pnx * elem_bytes, (cuuint64_t)g.plane * elem_bytes};
     cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 1};
     cuuint32_t estr[3] = {1, 1, 1};
-    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, estr,
+    const CUtensorMapDataType dt =
+        elem_bytes == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_UINT16;
+    CUresult r = enc(map, dt, 3, base, dims, strides, box, estr,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(WS_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
@@ -280,6 +291,49 @@ int upload_profiles(ws_t ws) {
     return WS_OK;
 }
 
+// The tile of the 16-bit streaming kernel.
+constexpr int kTile16X = 64, kTile16Y = 8;
+
+int encode_maps16(ws_t ws) {
+    const ws::Geom &g = ws->g;
+    int rc = WS_OK;
+    for (int b = 0; b < 2 && rc == WS_OK; ++b) {
+        rc = encode_map(&ws->t16_halo[b], ws->buf16[b], g, kTile16X + 16, kTile16Y + 2 * ws::kHalo, 2);
+        if (rc == WS_OK) rc = encode_map(&ws->t16_tile[b], ws->buf16[b], g, kTile16X, kTile16Y, 2);
+    }
+    if (rc == WS_OK) rc = encode_map(&ws->t16_w, ws->w, g, kTile16X, kTile16Y, 4);
+    return rc;
+}
+
+// FP32 buffers -> 16-bit buffers (both levels), exponent slots of the step.
+int encode_state16(ws_t ws) {
+    const int sn = (int)(ws->step & 3), sp = (int)((ws->step + 3) & 3);
+    WS_CUDA(ws::launch_encode16(ws->storage, ws->buf[ws->cur], ws->buf16[ws->cur], ws->g, ws->scale,
+                                sn, ws->stream),
+            "encode field");
+    WS_CUDA(ws::launch_encode16(ws->storage, ws->buf[1 - ws->cur], ws->buf16[1 - ws->cur], ws->g,
+                                ws->scale, sp, ws->stream),
+            "encode field");
+    // the next step accumulates max |u^{n+1}| into slot (step + 1) & 3
+    WS_CUDA(cudaMemsetAsync(&ws->scale->amax[(ws->step + 1) & 3], 0, sizeof(unsigned), ws->stream),
+            "encode field");
+    ws->launches += 4;
+    return WS_OK;
+}
+
+// 16-bit buffers -> FP32 buffers (both levels).
+int decode_state16(ws_t ws) {
+    const int sn = (int)(ws->step & 3), sp = (int)((ws->step + 3) & 3);
+    WS_CUDA(ws::launch_decode16(ws->storage, ws->buf16[ws->cur], ws->buf[ws->cur], ws->g, ws->scale,
+                                sn, ws->stream),
+            "decode field");
+    WS_CUDA(ws::launch_decode16(ws->storage, ws->buf16[1 - ws->cur], ws->buf[1 - ws->cur], ws->g,
+                                ws->scale, sp, ws->stream),
+            "decode field");
+    ws->launches += 2;
+    return WS_OK;
+}
+
 void destroy(ws_t ws) {
     if (!ws) return;
     cudaStreamSynchronize(ws->stream);
@@ -291,6 +345,9 @@ void destroy(ws_t ws) {
     cudaFree(ws->gz);
     cudaFree(ws->status);
     cudaFree(ws->energy);
+    cudaFree(ws->buf16[0]);
+    cudaFree(ws->buf16[1]);
+    cudaFree(ws->scale);
     free_receivers(ws);
     delete ws;
 }
@@ -385,6 +442,7 @@ int ws_set_velocity(ws_t ws, const float *v, int on_device) {
     if (c > cfl_limit())
         return fail(WS_ERR_CFL, "ws_set_velocity: max(V) dt / h = %.6f exceeds the limit %.6f", c,
                     cfl_limit());
+    ws->wmax = c * c;
     ws->vel_ok = true;
     return WS_OK;
 }
@@ -452,6 +510,42 @@ int ws_set_receivers(ws_t ws, int nrec, const int *ijk, int nt_max) {
     return WS_OK;
 }
 
+int ws_set_storage(ws_t ws, int storage) {
+    if (!ws) return fail(WS_ERR_BADARG, "ws_set_storage: NULL handle");
+    if (storage != WS_STORAGE_FP32 && storage != WS_STORAGE_BF16 && storage != WS_STORAGE_FP16)
+        return fail(WS_ERR_BADARG, "ws_set_storage: unknown storage %d", storage);
+    if (storage == ws->storage) return WS_OK;
+    if (storage != WS_STORAGE_FP32 && (ws->g.nx < kTile16X || ws->g.ny < kTile16Y))
+        return fail(WS_ERR_BADARG,
+                    "ws_set_storage: 16-bit storage needs nx >= %d and ny >= %d (grid %d x %d)",
+                    kTile16X, kTile16Y, ws->g.nx, ws->g.ny);
+    // bring the state to FP32 first
+    if (ws->storage != WS_STORAGE_FP32) {
+        int rc = decode_state16(ws);
+        if (rc != WS_OK) return rc;
+    }
+    if (storage != WS_STORAGE_FP32) {
+        const size_t hb = size_t(ws->g.pnx) * ws->g.pny * ws->g.pnz * sizeof(uint16_t);
+        for (int b = 0; b < 2; ++b)
+            if (!ws->buf16[b]) {
+                WS_CUDA(cudaMalloc(&ws->buf16[b], hb), "cudaMalloc 16-bit field");
+                WS_CUDA(cudaMemsetAsync(ws->buf16[b], 0, hb, ws->stream), "zero 16-bit field");
+            }
+        if (!ws->scale) {
+            WS_CUDA(cudaMalloc(&ws->scale, sizeof(ws::Scale16)), "cudaMalloc scales");
+            WS_CUDA(cudaMemsetAsync(ws->scale, 0, sizeof(ws::Scale16), ws->stream), "zero scales");
+        }
+        int rc = encode_maps16(ws);
+        if (rc != WS_OK) return rc;
+        ws->storage = storage;
+        rc = encode_state16(ws);
+        if (rc != WS_OK) return rc;
+    } else {
+        ws->storage = storage;
+    }
+    return WS_OK;
+}
+
 int ws_set_kernel(ws_t ws, int kernel, int tile_x, int tile_y, int zblock) {
     if (!ws) return fail(WS_ERR_BADARG, "ws_set_kernel: NULL handle");
     if (kernel != WS_KERNEL_AUTO && kernel != WS_KERNEL_DIRECT && kernel != WS_KERNEL_STREAM)
@@ -488,8 +582,15 @@ int ws_step(ws_t ws, int nsteps) {
                         ws->nt_max, ws->trace_start, ws->step, ws->step + nsteps - 1);
     }
     ws::StreamTiling tiling{};
-    const int kern = pick_kernel(ws, &tiling);
-    if (kern == WS_KERNEL_STREAM) {
+    const int kern = ws->storage != WS_STORAGE_FP32 ? WS_KERNEL_STREAM : pick_kernel(ws, &tiling);
+    if (ws->storage != WS_STORAGE_FP32) {
+        tiling.tx = kTile16X;
+        tiling.ty = kTile16Y;
+        tiling.zb = ws->tiling.zb > 0 ? ws->tiling.zb : default_zblock(ws->g.nz);
+        int rc = build_rec_tiles(ws, tiling);
+        if (rc != WS_OK) return rc;
+    }
+    if (kern == WS_KERNEL_STREAM && ws->storage == WS_STORAGE_FP32) {
         if (tiling.tx != ws->tiling.tx || tiling.ty != ws->tiling.ty) {
             ws->tiling.tx = tiling.tx;
             ws->tiling.ty = tiling.ty;
@@ -502,7 +603,6 @@ int ws_step(ws_t ws, int nsteps) {
     ws::StepArgs a{};
     a.g = ws->g;
     const double h2 = ws->h * ws->h;
-    a.c.c0x3 = (float)(3.0 * kW0);
     a.c.c1 = (float)kW1;
     a.c.c2 = (float)kW2;
     a.c.c3 = (float)kW3;
@@ -524,7 +624,17 @@ int ws_step(ws_t ws, int nsteps) {
         float *u = ws->buf[ws->cur];
         float *up = ws->buf[1 - ws->cur];
         cudaError_t e;
-        if (kern == WS_KERNEL_STREAM) {
+        if (ws->storage != WS_STORAGE_FP32) {
+            double hint = 0.0;
+            for (int q = 0; q < a.src.n; ++q)
+                hint = std::max(hint, std::fabs((double)a.src.s[q].amp) * ws->wmax);
+            e = ws::launch_step_stream16(ws->storage, &ws->t16_halo[ws->cur],
+                                         &ws->t16_tile[1 - ws->cur], &ws->t16_w, ws->buf16[1 - ws->cur],
+                                         a, ws->scale, ws->step, (float)hint, tiling,
+                                         ws->nrec > 0 ? ws->rec_ptr : nullptr, ws->rec_entries,
+                                         ws->stream);
+            ws->launches++;
+        } else if (kern == WS_KERNEL_STREAM) {
             e = ws::launch_step_stream(&ws->tmap_halo[ws->cur], &ws->tmap_tile[1 - ws->cur],
                                        &ws->tmap_w, up, a, tiling,
                                        ws->nrec > 0 ? ws->rec_ptr : nullptr, ws->rec_entries,
@@ -560,6 +670,10 @@ int ws_read_traces(ws_t ws, float *out, int on_device) {
 int ws_read_field(ws_t ws, float *u, float *u_prev, int on_device) {
     if (!ws) return fail(WS_ERR_BADARG, "ws_read_field: NULL handle");
     int rc = WS_OK;
+    if (ws->storage != WS_STORAGE_FP32) {
+        rc = decode_state16(ws);
+        if (rc != WS_OK) return rc;
+    }
     if (u) rc = copy_out(ws, u, ws->buf[ws->cur], on_device);
     if (rc == WS_OK && u_prev) rc = copy_out(ws, u_prev, ws->buf[1 - ws->cur], on_device);
     if (rc != WS_OK) return rc;
@@ -580,8 +694,12 @@ int ws_write_field(ws_t ws, const float *u, const float *u_prev, long long step,
             if (rc != WS_OK) return rc;
         }
     }
-    if (!on_device) WS_CUDA(cudaStreamSynchronize(ws->stream), "ws_write_field");
     ws->step = step;
+    if (ws->storage != WS_STORAGE_FP32) {
+        int rc = encode_state16(ws);
+        if (rc != WS_OK) return rc;
+    }
+    if (!on_device) WS_CUDA(cudaStreamSynchronize(ws->stream), "ws_write_field");
     return WS_OK;
 }
 
@@ -606,6 +724,10 @@ int ws_synchronize(ws_t ws) {
 int ws_energy(ws_t ws, double *e) {
     if (!ws || !e) return fail(WS_ERR_BADARG, "ws_energy: NULL argument");
     if (!ws->vel_ok) return fail(WS_ERR_STATE, "ws_energy: no valid velocity model");
+    if (ws->storage != WS_STORAGE_FP32) {
+        int rc = decode_state16(ws);
+        if (rc != WS_OK) return rc;
+    }
     const ws::Coeffs64 c{kW0, kW1, kW2, kW3, kW4};
     const long long np = ws::energy_partial_count(ws->g.ny, ws->g.nz);
     WS_CUDA(ws::launch_energy_padded(ws->buf[ws->cur], ws->buf[1 - ws->cur], ws->w, ws->g, ws->h, c,

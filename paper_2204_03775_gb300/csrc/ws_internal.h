@@ -19,10 +19,15 @@ constexpr unsigned kStatusTimeout = 1u;
 // Bounded device waits give up after this many nanoseconds of %globaltimer.
 constexpr unsigned long long kWaitLimitNs = 1000000000ull;
 
-// Stencil weights of the 8th-order second difference (offsets 0..4), the
-// centre one already multiplied by 3 (one per axis, Section III-C-2).
+// Stencil weights c_1..c_4 of the 8th-order second difference. The kernels
+// evaluate sum_m c_m (s_m - 6 u), s_m the sum of the six neighbours at
+// distance m: the centre weight is implied as -6 sum_m c_m, so the operator
+// is exactly zero on a constant field whatever the rounding of the weights
+// to float (with a separately rounded centre weight the stencil sum is off
+// zero by ~2e-7, a mass term whose phase drift reached 1e-4 relative error
+// after 1000 steps).
 struct Coeffs {
-    float c0x3, c1, c2, c3, c4;
+    float c1, c2, c3, c4;
 };
 
 // The same weights in double precision, centre weight for one axis.
@@ -109,6 +114,30 @@ cudaError_t launch_step_stream(const CUtensorMap *tmap_u, const CUtensorMap *tma
                                const CUtensorMap *tmap_w, float *up, const StepArgs &a,
                                const StreamTiling &t, const int *rec_ptr, const RecEntry *rec,
                                cudaStream_t s);
+
+// ---- 16-bit field storage (WS_STORAGE_BF16 / WS_STORAGE_FP16) ----
+// Ring of per-field power-of-two exponents and maxima, indexed by step & 3:
+// the field u^n is stored as u^n * 2^exps[n & 3]; amax[n & 3] = max |u^n|
+// (float bits, true units), accumulated by the step that writes u^n.
+struct Scale16 {
+    int exps[4];
+    unsigned amax[4];
+};
+bool stream16_tiling_supported(int tx, int ty);
+// tmap_u: u^n (16-bit) with box (tx+16, ty+8, 1); tmap_up: u^{n-1} (16-bit)
+// and tmap_w: (V dt/h)^2 (FP32), both with box (tx, ty, 1). src_hint: bound
+// on |(V dt)^2 s(t_n)| of this step's sources (picks the output exponent
+// while the field is still zero).
+cudaError_t launch_step_stream16(int storage, const CUtensorMap *tmap_u, const CUtensorMap *tmap_up,
+                                 const CUtensorMap *tmap_w, uint16_t *up, const StepArgs &a,
+                                 Scale16 *sc, long long step, float src_hint,
+                                 const StreamTiling &t, const int *rec_ptr, const RecEntry *rec,
+                                 cudaStream_t s);
+// FP32 padded field <-> 16-bit padded field (interior), exponent slot `slot`.
+cudaError_t launch_encode16(int storage, const float *f, uint16_t *out, const Geom &g, Scale16 *sc,
+                            int slot, cudaStream_t s);
+cudaError_t launch_decode16(int storage, const uint16_t *in, float *f, const Geom &g,
+                            const Scale16 *sc, int slot, cudaStream_t s);
 
 // Discrete energy (FP64): partial sums per (row block, plane) into
 // partials[energy_partial_count(ny, nz)], then their fixed-order sum into *out.

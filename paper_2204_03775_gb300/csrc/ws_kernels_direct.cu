@@ -31,11 +31,14 @@ __global__ void __launch_bounds__(256) step_direct_kernel(const float *__restric
         s[m] = ((u[p + m] + u[p - m]) + (u[p + m * sy] + u[p - m * sy])) +
                (u[p + m * sz] + u[p - m * sz]);
     }
-    float lap = a.c.c4 * s[4];
-    lap = fmaf(a.c.c3, s[3], lap);
-    lap = fmaf(a.c.c2, s[2], lap);
-    lap = fmaf(a.c.c1, s[1], lap);
-    lap = fmaf(a.c.c0x3, uc, lap);
+    // sum_m c_m (s_m - 6 u): exactly zero on constants (see Coeffs)
+    float d[5];
+#pragma unroll
+    for (int m = 1; m <= 4; ++m) d[m] = fmaf(-6.0f, uc, s[m]);
+    float lap = a.c.c4 * d[4];
+    lap = fmaf(a.c.c3, d[3], lap);
+    lap = fmaf(a.c.c2, d[2], lap);
+    lap = fmaf(a.c.c1, d[1], lap);
 
     const float wc = w[p];
     const float gd = a.gx[i] * a.gy[j] * a.gz[k];
