@@ -49,6 +49,8 @@ def parse_args():
     ap.add_argument("--zblock", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-storage16", action="store_true",
+                    help="skip the BF16/FP16 storage timings and errors")
     return ap.parse_args()
 
 
@@ -170,6 +172,65 @@ def cpu_baseline(w, target_s=15.0):
             "sample": f"FP64 oracle, top slab k in [0,{depth}) of the {w.nx}x{w.ny}x{w.nz} "
                       f"survey (same model, taper, source), {steps} steps from rest, "
                       f"{el:.1f} s wall"}
+
+
+def storage16_report(w, K, W, stream, peak):
+    """Throughput of the 16-bit storage modes on the same survey, and their
+    error against the FP32 path (itself within 3e-6 of the FP64 oracle after
+    1000 steps on 256^3) at steps 100, 500 and 1000, evaluated on the device."""
+    import torch
+    import paper_2204_03775_gb300 as wsb
+
+    def make(storage, nt_max):
+        h = wsb.ws_create(w.nx, w.ny, w.nz, w.h, w.dt)
+        wsb.ws_set_stream(h, stream)
+        wsb.ws_set_storage(h, storage)
+        wsb.ws_set_velocity(h, w.vel)
+        wsb.ws_set_sponge(h, *w.sponge)
+        for s in w.sources:
+            wsb.ws_add_source(h, *s)
+        wsb.ws_set_receivers(h, w.receivers, nt_max)
+        return h
+
+    out = {}
+    modes = [("bf16", wsb.WS_STORAGE_BF16), ("fp16", wsb.WS_STORAGE_FP16)]
+    for name, st in modes:
+        h = make(st, K + W)
+        wsb.ws_step(h, W)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        wsb.ws_step(h, K)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        wsb.ws_synchronize(h)
+        sec = e0.elapsed_time(e1) / 1e3 / K
+        out[name] = {"value": w.points / sec / 1e9, "unit": UNIT, "ms_per_step": 1e3 * sec,
+                     "bytes_per_point": 10, "roofline_frac": 10 * w.points / sec / 1e9 / peak}
+        wsb.ws_destroy(h)
+
+    checkpoints = [100, 500, 1000]
+    hs = {name: make(st, checkpoints[-1]) for name, st in [("fp32", wsb.WS_STORAGE_FP32)] + modes}
+    bufs = {name: torch.empty((w.nz, w.ny, w.nx), dtype=torch.float32, device="cuda") for name in hs}
+    errs = {name: [] for name, _ in modes}
+    done = 0
+    for c in checkpoints:
+        for name, h in hs.items():
+            wsb.ws_step(h, c - done)
+            wsb.ws_read_field(h, bufs[name], None)
+        torch.cuda.synchronize()
+        ref = bufs["fp32"].double()
+        nref = torch.linalg.vector_norm(ref).item()
+        for name, _ in modes:
+            d = torch.linalg.vector_norm(bufs[name].double() - ref).item()
+            errs[name].append(d / nref)
+        done = c
+    for name, _ in modes:
+        out[name]["rel_l2_vs_fp32_at_steps"] = dict(zip(map(str, checkpoints), errs[name]))
+    for h in hs.values():
+        wsb.ws_destroy(h)
+    return out
 
 
 def run_reference(args):
@@ -332,6 +393,8 @@ def main():
         "e2e": e2e,
     }
     wsb.ws_destroy(h)
+    if world == 1 and not args.no_storage16 and n >= 64:
+        line["storage16"] = storage16_report(w, K, W, stream, peak)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w)
     print(json.dumps(line), flush=True)

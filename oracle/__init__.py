@@ -80,9 +80,16 @@ def _load():
         ctypes.c_int, ip, dp,
         ctypes.c_int, ip, ctypes.c_int, ctypes.c_longlong,
         dp, dp, ctypes.c_int,
-        ip,
+        ip, dp,
         dp, dp, dp]
     lib.or_run.restype = ctypes.c_int
+    lib.or_adjoint_gradient.argtypes = [
+        ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, dp,
+        dp, ctypes.c_int, ctypes.c_double,
+        ctypes.c_int, ip, dp, dp,
+        ctypes.c_int, ip, ctypes.c_int, dp,
+        dp, dp, dp, dp]
+    lib.or_adjoint_gradient.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -177,7 +184,7 @@ def cerjan(n: int, nb: int, a: float) -> np.ndarray:
 def run(vel: np.ndarray, h: float, dt: float, nt: int, *,
         sources=(), receivers=None, sponge=(0, 0.0), n0: int = 0,
         u_init=None, uprev_init=None, periodic: bool = False,
-        window=None, coeffs=None) -> dict:
+        window=None, coeffs=None, source_series=None) -> dict:
     """Algorithm 1 / Eq. 2 for nt steps; see ``or_run`` in wave_oracle.c.
 
     vel        [nz][ny][nx] velocity of the computed box (float64 copy taken)
@@ -186,6 +193,7 @@ def run(vel: np.ndarray, h: float, dt: float, nt: int, *,
     sponge     (nb, a) Cerjan width and strength; nb = 0 disables it
     window     None, or (ox, oy, oz, NX, NY, NZ): the box is a window of a
                larger grid (exact while the wavefield stays inside it)
+    source_series  None, or [nsrc][nt]: each source's f^n, replacing the Ricker
     Returns dict(traces=[nrec][nt], u=u^{n0+nt}, u_prev=u^{n0+nt-1}).
     """
     vel = np.ascontiguousarray(vel, dtype=np.float64)
@@ -204,13 +212,52 @@ def run(vel: np.ndarray, h: float, dt: float, nt: int, *,
     ui = None if u_init is None else np.ascontiguousarray(u_init, dtype=np.float64)
     upi = None if uprev_init is None else np.ascontiguousarray(uprev_init, dtype=np.float64)
     win = None if window is None else np.ascontiguousarray(np.array(window, dtype=np.int32))
+    ser = None
+    if source_series is not None:
+        ser = np.ascontiguousarray(np.asarray(source_series, np.float64).reshape(nsrc, nt))
     rc = _load().or_run(nx, ny, nz, float(h), float(dt), _dptr(c),
                         _dptr(vel), int(sponge[0]), float(sponge[1]),
                         nsrc, _iptr(src_ijk), _dptr(src_par),
                         nrec, _iptr(rec), int(nt), int(n0),
                         _dptr(ui), _dptr(upi), int(bool(periodic)),
-                        _iptr(win),
+                        _iptr(win), _dptr(ser),
                         _dptr(traces), _dptr(u_out), _dptr(up_out))
     if rc != 0:
         raise ValueError("oracle run rejected its arguments")
     return {"traces": traces, "u": u_out, "u_prev": up_out}
+
+
+def adjoint_gradient(vel: np.ndarray, h: float, dt: float, nt: int, d_obs: np.ndarray, *,
+                     sources=(), receivers=None, sponge=(0, 0.0), source_series=None,
+                     coeffs=None) -> dict:
+    """Misfit 1/2 |traces - d_obs|^2 of a run from rest and its gradient with
+    respect to the squared slowness m = 1/V^2 (see or_adjoint_gradient).
+
+    Returns dict(misfit, grad_m [nz][ny][nx], traces [nrec][nt],
+    dj_dsrc [nsrc][nt] = dJ/d(source function sample)).
+    """
+    vel = np.ascontiguousarray(vel, dtype=np.float64)
+    nz, ny, nx = vel.shape
+    c = coefficients_f64() if coeffs is None else np.ascontiguousarray(coeffs, dtype=np.float64)
+    src = list(sources)
+    nsrc = len(src)
+    src_ijk = np.ascontiguousarray(np.array([s[:3] for s in src], dtype=np.int32).reshape(nsrc, 3))
+    src_par = np.ascontiguousarray(np.array([s[3:] for s in src], dtype=np.float64).reshape(nsrc, 3))
+    rec = np.ascontiguousarray(np.asarray(receivers, np.int32).reshape(-1, 3))
+    nrec = rec.shape[0]
+    dob = np.ascontiguousarray(np.asarray(d_obs, np.float64).reshape(nrec, nt))
+    ser = None
+    if source_series is not None:
+        ser = np.ascontiguousarray(np.asarray(source_series, np.float64).reshape(nsrc, nt))
+    misfit = ctypes.c_double()
+    grad = np.zeros((nz, ny, nx), np.float64)
+    traces = np.zeros((nrec, nt), np.float64)
+    djds = np.zeros((nsrc, nt), np.float64)
+    rc = _load().or_adjoint_gradient(nx, ny, nz, float(h), float(dt), _dptr(c), _dptr(vel),
+                                     int(sponge[0]), float(sponge[1]), nsrc, _iptr(src_ijk),
+                                     _dptr(src_par), _dptr(ser), nrec, _iptr(rec), int(nt),
+                                     _dptr(dob), ctypes.byref(misfit), _dptr(grad),
+                                     _dptr(traces), _dptr(djds))
+    if rc != 0:
+        raise ValueError("oracle adjoint rejected its arguments")
+    return {"misfit": misfit.value, "grad_m": grad, "traces": traces, "dj_dsrc": djds}

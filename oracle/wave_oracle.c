@@ -161,6 +161,8 @@ double or_ricker(double t, double f0, double t0, double amp)
  *   c          5 coefficients c_0..c_4 (unscaled; divided by h^2 here)
  *   nb, a      Cerjan width (cells) and strength; nb = 0 disables damping
  *   src_ijk    [nsrc][3] global source cells; src_par [nsrc][3] = f0, t0, amp
+ *   src_series NULL, or [nsrc][nt]: the source function f^{n0+n} of each
+ *              source, used instead of the Ricker wavelet
  *   rec_ijk    [nrec][3] global receiver cells
  *   nt         number of steps; n0 = global index of the first step
  *   u_init, uprev_init   initial u^{n0}, u^{n0-1} of the box (NULL = zero)
@@ -174,7 +176,7 @@ int or_run(int nx, int ny, int nz, double h, double dt, const double *c,
            int nsrc, const int *src_ijk, const double *src_par,
            int nrec, const int *rec_ijk, int nt, long long n0,
            const double *u_init, const double *uprev_init, int periodic,
-           const int *win,
+           const int *win, const double *src_series,
            double *traces, double *u_out, double *uprev_out)
 {
     if (nx < 1 || ny < 1 || nz < 1 || nt < 0 || h <= 0.0 || dt <= 0.0)
@@ -243,7 +245,8 @@ int or_run(int nx, int ny, int nz, double h, double dt, const double *c,
         for (int s = 0; s < nsrc; ++s) {
             int i = src_ijk[3 * s] - ox, j = src_ijk[3 * s + 1] - oy, k = src_ijk[3 * s + 2] - oz;
             double v = vel[uidx(i, j, k, nx, ny)];
-            double f = or_ricker(t, src_par[3 * s], src_par[3 * s + 1], src_par[3 * s + 2]);
+            double f = src_series ? src_series[(size_t)s * (size_t)nt + (size_t)n]
+                                  : or_ricker(t, src_par[3 * s], src_par[3 * s + 1], src_par[3 * s + 2]);
             u_next[pidx(i, j, k, nx, ny)] += (v * dt) * (v * dt) * f;
         }
 
@@ -268,5 +271,140 @@ int or_run(int nx, int ny, int nz, double h, double dt, const double *c,
             }
 
     free(u_prev); free(u_cur); free(u_next); free(gx); free(gy); free(gz);
+    return 0;
+}
+
+/*
+ * Misfit J = 1/2 sum_r sum_n (u^{n+1}[rec_r] - d_obs[r][n])^2 of a run from
+ * rest (nt steps, Eq. 2 with the taper and sources as in or_run, zero
+ * Dirichlet halo) and its exact discrete gradient with respect to the
+ * squared slowness m = 1/V^2 of every cell, by the adjoint (Lagrange
+ * multiplier) recurrence of the step equations. The paper has no adjoint;
+ * this is the build's extension, written in the plain multiplier form.
+ *
+ * With W = (V dt)^2, G the taper, A = G (2 + W L), B = G^2 and the step
+ * u^{n+1} = A u^n - B u^{n-1} + f^n (f^n = W_s s_n at the source cell), the
+ * multipliers obey, for k = nt .. 1 with lambda^{nt+1} = lambda^{nt+2} = 0,
+ *     lambda^k = A^T lambda^{k+1} - B^T lambda^{k+2} + r^k,
+ *     A^T lambda = 2 G lambda + L (W G lambda),   B^T lambda = G^2 lambda,
+ * r^k = dJ/du^k = sum_r (u^k[rec_r] - d_obs[r][k-1]) e_{rec_r}; and
+ *     dJ/dW_i = sum_n lambda^{n+1}_i (G_i (L u^n)_i + [i = s] s_n),
+ *     dJ/dm_i = dJ/dW_i * dW_i/dm_i = -W_i V_i^2 dJ/dW_i.
+ * Every forward state is kept (small grids only).
+ *
+ * Outputs: *misfit; grad_m [nz][ny][nx]; traces [nrec][nt] (may be NULL);
+ * dj_dsrc [nsrc][nt] = dJ/ds_n = lambda^{n+1}_s W_s (may be NULL), the
+ * adjoint of the map from source functions to traces.
+ * Returns 0, or -1 on a bad argument or a failed allocation.
+ */
+int or_adjoint_gradient(int nx, int ny, int nz, double h, double dt, const double *c,
+                        const double *vel, int nb, double a,
+                        int nsrc, const int *src_ijk, const double *src_par,
+                        const double *src_series,
+                        int nrec, const int *rec_ijk, int nt, const double *d_obs,
+                        double *misfit, double *grad_m, double *traces, double *dj_dsrc)
+{
+    if (nx < 1 || ny < 1 || nz < 1 || nt < 1 || nrec < 1 || h <= 0.0 || dt <= 0.0)
+        return -1;
+    size_t np = padded_size(nx, ny, nz), nc = (size_t)nx * ny * nz;
+    double *states = calloc(np * (size_t)(nt + 2), sizeof(double));  /* u^{-1}, u^0 .. u^nt */
+    double *lam = calloc(np * 3, sizeof(double));                  /* lambda^{k}, ^{k+1}, ^{k+2} */
+    double *q = calloc(np, sizeof(double));
+    double *w = malloc(sizeof(double) * nc), *g = malloc(sizeof(double) * nc);
+    double *gw = calloc(nc, sizeof(double));
+    double *tr = malloc(sizeof(double) * (size_t)nrec * nt);
+    if (!states || !lam || !q || !w || !g || !gw || !tr) {
+        free(states); free(lam); free(q); free(w); free(g); free(gw); free(tr);
+        return -1;
+    }
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                size_t o = uidx(i, j, k, nx, ny);
+                w[o] = (vel[o] * dt) * (vel[o] * dt);
+                g[o] = or_cerjan(i, nx, nb, a) * or_cerjan(j, ny, nb, a) * or_cerjan(k, nz, nb, a);
+            }
+#define STATE(n) (states + np * (size_t)((n) + 1))   /* u^n, n = -1 .. nt */
+
+    /* forward, keeping every state */
+    for (int n = 0; n < nt; ++n) {
+        double *um = STATE(n - 1), *u = STATE(n), *un = STATE(n + 1);
+#pragma omp parallel for schedule(static)
+        for (int k = 0; k < nz; ++k)
+            for (int j = 0; j < ny; ++j)
+                for (int i = 0; i < nx; ++i) {
+                    size_t p = pidx(i, j, k, nx, ny), o = uidx(i, j, k, nx, ny);
+                    double L = lap_at(u, i, j, k, nx, ny, h, c);
+                    un[p] = g[o] * (2.0 * u[p] - g[o] * um[p] + w[o] * L);
+                }
+        for (int s = 0; s < nsrc; ++s) {
+            int i = src_ijk[3 * s], j = src_ijk[3 * s + 1], k = src_ijk[3 * s + 2];
+            double f = src_series ? src_series[(size_t)s * nt + n]
+                                  : or_ricker(n * dt, src_par[3 * s], src_par[3 * s + 1],
+                                              src_par[3 * s + 2]);
+            un[pidx(i, j, k, nx, ny)] += w[uidx(i, j, k, nx, ny)] * f;
+        }
+        for (int r = 0; r < nrec; ++r)
+            tr[(size_t)r * nt + n] = un[pidx(rec_ijk[3 * r], rec_ijk[3 * r + 1], rec_ijk[3 * r + 2], nx, ny)];
+    }
+    double J = 0.0;
+    for (size_t t = 0; t < (size_t)nrec * nt; ++t) {
+        double d = tr[t] - d_obs[t];
+        J += 0.5 * d * d;
+    }
+
+    /* backward: lambda^k for k = nt .. 1 (rotating three buffers) */
+    double *lk2 = lam, *lk1 = lam + np, *lk = lam + 2 * np;   /* ^{k+2}, ^{k+1}, ^k */
+    for (int kk = nt; kk >= 1; --kk) {
+        /* q = W G lambda^{k+1} on the padded grid, zero halo */
+        for (int k = 0; k < nz; ++k)
+            for (int j = 0; j < ny; ++j)
+                for (int i = 0; i < nx; ++i) {
+                    size_t p = pidx(i, j, k, nx, ny), o = uidx(i, j, k, nx, ny);
+                    q[p] = w[o] * g[o] * lk1[p];
+                }
+#pragma omp parallel for schedule(static)
+        for (int k = 0; k < nz; ++k)
+            for (int j = 0; j < ny; ++j)
+                for (int i = 0; i < nx; ++i) {
+                    size_t p = pidx(i, j, k, nx, ny), o = uidx(i, j, k, nx, ny);
+                    lk[p] = 2.0 * g[o] * lk1[p] + lap_at(q, i, j, k, nx, ny, h, c)
+                            - g[o] * g[o] * lk2[p];
+                }
+        for (int r = 0; r < nrec; ++r) {
+            size_t p = pidx(rec_ijk[3 * r], rec_ijk[3 * r + 1], rec_ijk[3 * r + 2], nx, ny);
+            lk[p] += tr[(size_t)r * nt + (kk - 1)] - d_obs[(size_t)r * nt + (kk - 1)];
+        }
+        /* lambda^k = lambda^{n+1} with n = kk - 1: gradient terms of step n */
+        {
+            const int n = kk - 1;
+            double *u = STATE(n);
+#pragma omp parallel for schedule(static)
+            for (int k = 0; k < nz; ++k)
+                for (int j = 0; j < ny; ++j)
+                    for (int i = 0; i < nx; ++i) {
+                        size_t p = pidx(i, j, k, nx, ny), o = uidx(i, j, k, nx, ny);
+                        gw[o] += lk[p] * g[o] * lap_at(u, i, j, k, nx, ny, h, c);
+                    }
+            for (int s = 0; s < nsrc; ++s) {
+                int i = src_ijk[3 * s], j = src_ijk[3 * s + 1], k = src_ijk[3 * s + 2];
+                size_t p = pidx(i, j, k, nx, ny), o = uidx(i, j, k, nx, ny);
+                double f = src_series ? src_series[(size_t)s * nt + n]
+                                      : or_ricker(n * dt, src_par[3 * s], src_par[3 * s + 1],
+                                                  src_par[3 * s + 2]);
+                gw[o] += lk[p] * f;
+                if (dj_dsrc) dj_dsrc[(size_t)s * nt + n] = lk[p] * w[o];
+            }
+        }
+        double *tmp = lk2;
+        lk2 = lk1;
+        lk1 = lk;
+        lk = tmp;
+    }
+#undef STATE
+    for (size_t o = 0; o < nc; ++o) grad_m[o] = -w[o] * vel[o] * vel[o] * gw[o];
+    *misfit = J;
+    if (traces) memcpy(traces, tr, sizeof(double) * (size_t)nrec * nt);
+    free(states); free(lam); free(q); free(w); free(g); free(gw); free(tr);
     return 0;
 }
