@@ -65,6 +65,10 @@ extern "C" {
 
 #define WS_MAX_SOURCES   16
 
+/* What ws_adjoint_gradient's data array holds. */
+#define WS_ADJ_DATA       0  /* observed traces d: residual = traces - d */
+#define WS_ADJ_RESIDUAL   1  /* the residual itself, dJ/dtraces of any J */
+
 typedef struct ws_handle *ws_t;
 
 /* Create a stepper for an nx x ny x nz grid with spacing h (m) and time step
@@ -91,6 +95,12 @@ int ws_set_stream(ws_t ws, void *cuda_stream);
  * then no longer valid and ws_step fails until a valid one is set).
  * Synchronizes the stream (it reads back the model's extrema). */
 int ws_set_velocity(ws_t ws, const float *v, int on_device);
+
+/* Set the model as squared slowness m = 1 / V^2 (s^2/m^2), [nz][ny][nx]:
+ * the library stores (V dt / h)^2 = (dt / h)^2 / m. Same checks and
+ * errors as ws_set_velocity, with max(V) = 1 / sqrt(min(m)). The paper has
+ * no inversion; m is the parameter ws_adjoint_gradient differentiates by. */
+int ws_set_slowness2(ws_t ws, const float *m, int on_device);
 
 /* Absorbing taper (Cerjan et al. 1985): for a cell at distance d < nb cells
  * from the nearer outer face of an axis, that axis contributes
@@ -176,6 +186,38 @@ int ws_energy(ws_t ws, double *e);
 #define WS_NOALLOC_MAX_PARTIALS 32768
 int ws_energy_noalloc(const float *u, const float *u_prev, const float *v, int nx, int ny, int nz,
                       double h, double dt, double *e, void *cuda_stream);
+
+/* Gradient of a trace misfit with respect to the squared slowness m = 1/V^2
+ * of every cell, by the discrete adjoint of the stepper (exact up to float
+ * rounding: the derivative of the very recurrence ws_step computes,
+ * taper and sources included). The paper solves only the forward problem
+ * (Section II); this is the inversion use of its stepper.
+ *
+ * The call runs the forward problem from rest: fields zeroed, step 0, the
+ * handle's sources, nt_max steps, traces recorded as by ws_step. With
+ * mode = WS_ADJ_DATA, data is the observed traces d and the residual is
+ * r = traces - d, J = |r|^2 / 2; with WS_ADJ_RESIDUAL, data is r itself
+ * (any upstream dJ/dtraces) and J is reported as |r|^2 / 2. data is
+ * [nrec][nt_max] float32 like ws_read_traces. grad_m receives dJ/dm,
+ * [nz][ny][nx] float32; *misfit (host, may be NULL) receives J in double.
+ *
+ * Method: with lambda the multipliers of the step equations, rho = W G
+ * lambda (W = (V dt/h)^2, G the taper) obeys the forward recurrence run
+ * backwards, rho^k = G (2 rho^{k+1} - G rho^{k+2} + W Lap' rho^{k+1}) +
+ * W G r^k (Lap' = h^2 Lap, r^k injected at the receivers), so the step
+ * kernels advance rho; dJ/dm = -V^2 sum_n rho^{n+1} (Lap' u^n), plus
+ * -V^2 sum_n rho^{n+1} h^2 s_n / G at each source cell. The states u^n are
+ * recomputed from ceil(N / C) - 1 checkpoint pairs, C = ceil(sqrt(N)),
+ * N = nt_max: two forward passes and one backward pass in all.
+ *
+ * Needs a velocity model, receivers and FP32 storage, else STATE. Device
+ * scratch, allocated for the call and freed before it returns: about
+ * 3 sqrt(N) + 3 padded fields, 8 bytes per cell, and two trace arrays.
+ * Afterwards the handle holds the forward run's final state (step N) and
+ * its traces. Synchronizes the stream. Errors: BADARG, STATE, OOM, CUDA,
+ * TIMEOUT. */
+int ws_adjoint_gradient(ws_t ws, const float *data, int mode, float *grad_m, double *misfit,
+                        int on_device);
 
 /* Store u^n and u^{n-1} in 16 bits (WS_STORAGE_BF16 or WS_STORAGE_FP16;
  * (V dt/h)^2 stays FP32: 10 bytes per cell update instead of 16) or back in

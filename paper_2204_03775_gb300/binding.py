@@ -34,6 +34,9 @@ WS_STORAGE_FP16 = 2
 
 WS_MAX_SOURCES = 16
 
+WS_ADJ_DATA = 0
+WS_ADJ_RESIDUAL = 1
+
 
 class WaveStepError(RuntimeError):
     def __init__(self, code: int, message: str):
@@ -66,6 +69,8 @@ def load_library(build_if_missing: bool = False):
         "ws_destroy": (i, [vp]),
         "ws_set_stream": (i, [vp, vp]),
         "ws_set_velocity": (i, [vp, vp, i]),
+        "ws_set_slowness2": (i, [vp, vp, i]),
+        "ws_adjoint_gradient": (i, [vp, vp, i, vp, ctypes.POINTER(d), i]),
         "ws_set_sponge": (i, [vp, i, d]),
         "ws_add_source": (i, [vp, i, i, i, d, d, d]),
         "ws_clear_sources": (i, [vp]),
@@ -157,6 +162,33 @@ def ws_set_stream(ws: Handle, stream) -> None:
 def ws_set_velocity(ws: Handle, v) -> None:
     p, dev = _ptr(v, ws.shape)
     _check(load_library().ws_set_velocity(ws.ptr, ctypes.c_void_p(p), dev), "ws_set_velocity")
+
+
+def ws_set_slowness2(ws: Handle, m) -> None:
+    p, dev = _ptr(m, ws.shape)
+    _check(load_library().ws_set_slowness2(ws.ptr, ctypes.c_void_p(p), dev), "ws_set_slowness2")
+
+
+def ws_adjoint_gradient(ws: Handle, data, mode: int = WS_ADJ_DATA, grad_m=None):
+    """(dJ/dm [nz][ny][nx], J) of the trace misfit; data [nrec][nt_max] float32.
+
+    grad_m (optional) receives the gradient; host and device arrays must not
+    be mixed. Returns (grad_m, misfit)."""
+    pd, dd = _ptr(data, (ws.nrec, ws.nt_max))
+    if grad_m is None:
+        if dd:
+            import torch
+            grad_m = torch.empty(ws.shape, dtype=torch.float32, device=data.device)
+        else:
+            grad_m = np.empty(ws.shape, np.float32)
+    pg, dg = _ptr(grad_m, ws.shape)
+    if dd != dg:
+        raise ValueError("data and grad_m must both be host or both be device arrays")
+    j = ctypes.c_double()
+    _check(load_library().ws_adjoint_gradient(ws.ptr, ctypes.c_void_p(pd), int(mode),
+                                              ctypes.c_void_p(pg), ctypes.byref(j), dd),
+           "ws_adjoint_gradient")
+    return grad_m, j.value
 
 
 def ws_set_sponge(ws: Handle, nb: int, a: float) -> None:

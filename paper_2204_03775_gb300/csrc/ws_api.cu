@@ -334,6 +334,79 @@ int decode_state16(ws_t ws) {
     return WS_OK;
 }
 
+// Point sources of step n: (V_s dt)^2 s(t_n) is added at each source cell,
+// i.e. amp = h^2 s(t_n) times the stored (V dt / h)^2.
+void sources_of_step(const ws_t ws, long long n, ws::Sources *out) {
+    out->n = (int)ws->src.size();
+    const double t = double(n) * ws->dt;
+    for (int q = 0; q < out->n; ++q) {
+        const SourceDef &d = ws->src[q];
+        out->s[q] = ws::SourceSample{d.i, d.j, d.k,
+                                     (float)(ws->h * ws->h * ricker(t, d.f0, d.t0, d.amp))};
+    }
+}
+
+// Step arguments common to every step of the handle's model.
+ws::StepArgs base_args(const ws_t ws) {
+    ws::StepArgs a{};
+    a.g = ws->g;
+    a.c.c1 = (float)kW1;
+    a.c.c2 = (float)kW2;
+    a.c.c3 = (float)kW3;
+    a.c.c4 = (float)kW4;
+    a.gx = ws->gx;
+    a.gy = ws->gy;
+    a.gz = ws->gz;
+    a.traces = ws->traces;
+    a.nt_max = ws->nt_max;
+    a.status = ws->status;
+    return a;
+}
+
+// One FP32 step of the handle's model (Eq. 1 discretised): out = u^{n+1}
+// from un = u^n (with its halo box map) and unm1 = u^{n-1} (with its tile box
+// map); out may be unm1. Adds the sources of step n when `sources`, records
+// the receivers' trace column n - trace_start when `record`.
+int step_fp32(ws_t ws, ws::StepArgs &a, int kern, const ws::StreamTiling &tiling, const float *un,
+              const CUtensorMap *un_halo, const float *unm1, const CUtensorMap *unm1_tile,
+              float *out, long long n, bool sources, bool record) {
+    if (sources)
+        sources_of_step(ws, n, &a.src);
+    else
+        a.src.n = 0;
+    a.trace_step = n - ws->trace_start;
+    cudaError_t e;
+    if (kern == WS_KERNEL_STREAM) {
+        e = ws::launch_step_stream(un_halo, unm1_tile, &ws->tmap_w, out, a, tiling,
+                                   record ? ws->rec_ptr : nullptr, ws->rec_entries, ws->stream);
+        ws->launches++;
+    } else {
+        e = ws::launch_step_direct(un, unm1, out, ws->w, a, ws->stream);
+        ws->launches++;
+        if (e == cudaSuccess && record) {
+            e = ws::launch_gather_receivers(out, ws->rec_pidx, ws->nrec, ws->traces, ws->nt_max,
+                                            a.trace_step, ws->stream);
+            ws->launches++;
+        }
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "step launch");
+    return WS_OK;
+}
+
+// Select the FP32 kernel for the next steps and bring the tensor maps and
+// the receiver table in line with its tiling.
+int prepare_fp32(ws_t ws, int *kern, ws::StreamTiling *tiling) {
+    *kern = pick_kernel(ws, tiling);
+    if (*kern != WS_KERNEL_STREAM) return WS_OK;
+    if (tiling->tx != ws->tiling.tx || tiling->ty != ws->tiling.ty) {
+        ws->tiling.tx = tiling->tx;
+        ws->tiling.ty = tiling->ty;
+        int rc = encode_maps(ws);
+        if (rc != WS_OK) return rc;
+    }
+    return build_rec_tiles(ws, *tiling);
+}
+
 void destroy(ws_t ws) {
     if (!ws) return;
     cudaStreamSynchronize(ws->stream);
@@ -350,6 +423,44 @@ void destroy(ws_t ws) {
     cudaFree(ws->scale);
     free_receivers(ws);
     delete ws;
+}
+
+
+// A padded FP32 field with the streaming kernel's two boxes on it.
+struct MappedField {
+    float *p = nullptr;
+    CUtensorMap halo, tile;
+};
+
+// Device scratch of one call: freed, after the stream drains, on every return.
+struct Scratch {
+    cudaStream_t stream;
+    std::vector<void *> ptrs;
+    explicit Scratch(cudaStream_t s) : stream(s) {}
+    ~Scratch() {
+        cudaStreamSynchronize(stream);
+        for (void *p : ptrs) cudaFree(p);
+    }
+    template <class T>
+    cudaError_t alloc(T **p, size_t bytes) {
+        void *q = nullptr;
+        cudaError_t e = cudaMalloc(&q, bytes);
+        if (e != cudaSuccess) return e;
+        ptrs.push_back(q);
+        *p = static_cast<T *>(q);
+        return cudaSuccess;
+    }
+};
+
+int alloc_field(ws_t ws, Scratch &sc, MappedField *f, bool maps, bool zero) {
+    const size_t fb = field_bytes(ws->g);
+    WS_CUDA(sc.alloc(&f->p, fb), "cudaMalloc adjoint field");
+    if (zero) WS_CUDA(cudaMemsetAsync(f->p, 0, fb, ws->stream), "zero adjoint field");
+    if (!maps) return WS_OK;
+    const int tx = ws->tiling.tx, ty = ws->tiling.ty;
+    int rc = encode_map(&f->halo, f->p, ws->g, tx + 2 * ws::kHalo, ty + 2 * ws::kHalo);
+    if (rc == WS_OK) rc = encode_map(&f->tile, f->p, ws->g, tx, ty);
+    return rc;
 }
 
 }  // namespace
@@ -441,6 +552,35 @@ int ws_set_velocity(ws_t ws, const float *v, int on_device) {
     const double c = double(vmax) * ws->dt / ws->h;
     if (c > cfl_limit())
         return fail(WS_ERR_CFL, "ws_set_velocity: max(V) dt / h = %.6f exceeds the limit %.6f", c,
+                    cfl_limit());
+    ws->wmax = c * c;
+    ws->vel_ok = true;
+    return WS_OK;
+}
+
+int ws_set_slowness2(ws_t ws, const float *m, int on_device) {
+    if (!ws || !m) return fail(WS_ERR_BADARG, "ws_set_slowness2: NULL argument");
+    ws->vel_ok = false;
+    int rc = copy_in(ws, ws->w, m, on_device);
+    if (rc != WS_OK) return rc;
+    static const unsigned init[2] = {0u, 0x7f800000u};
+    WS_CUDA(cudaMemcpyAsync(ws->status + 1, init, sizeof init, cudaMemcpyHostToDevice, ws->stream),
+            "ws_set_slowness2");
+    const double r = ws->dt / ws->h;
+    WS_CUDA(ws::launch_slowness2_to_w(ws->w, ws->g, r * r, ws->status + 1, ws->stream),
+            "slowness conversion kernel");
+    ws->launches++;
+    unsigned ext[2];
+    WS_CUDA(cudaMemcpyAsync(ext, ws->status + 1, sizeof ext, cudaMemcpyDeviceToHost, ws->stream),
+            "ws_set_slowness2");
+    WS_CUDA(cudaStreamSynchronize(ws->stream), "ws_set_slowness2");
+    float mmin;
+    std::memcpy(&mmin, &ext[1], 4);
+    if (ext[1] == 0u)
+        return fail(WS_ERR_BADARG, "ws_set_slowness2: every value must be finite and > 0");
+    const double c = ws->dt / (ws->h * std::sqrt(double(mmin)));   // max V dt / h
+    if (c > cfl_limit())
+        return fail(WS_ERR_CFL, "ws_set_slowness2: max(V) dt / h = %.6f exceeds the limit %.6f", c,
                     cfl_limit());
     ws->wmax = c * c;
     ws->vel_ok = true;
@@ -582,74 +722,38 @@ int ws_step(ws_t ws, int nsteps) {
                         ws->nt_max, ws->trace_start, ws->step, ws->step + nsteps - 1);
     }
     ws::StreamTiling tiling{};
-    const int kern = ws->storage != WS_STORAGE_FP32 ? WS_KERNEL_STREAM : pick_kernel(ws, &tiling);
+    int kern = WS_KERNEL_STREAM;
     if (ws->storage != WS_STORAGE_FP32) {
         tiling.tx = kTile16X;
         tiling.ty = kTile16Y;
         tiling.zb = ws->tiling.zb > 0 ? ws->tiling.zb : default_zblock(ws->g.nz);
         int rc = build_rec_tiles(ws, tiling);
         if (rc != WS_OK) return rc;
-    }
-    if (kern == WS_KERNEL_STREAM && ws->storage == WS_STORAGE_FP32) {
-        if (tiling.tx != ws->tiling.tx || tiling.ty != ws->tiling.ty) {
-            ws->tiling.tx = tiling.tx;
-            ws->tiling.ty = tiling.ty;
-            int rc = encode_maps(ws);
-            if (rc != WS_OK) return rc;
-        }
-        int rc = build_rec_tiles(ws, tiling);
+    } else {
+        int rc = prepare_fp32(ws, &kern, &tiling);
         if (rc != WS_OK) return rc;
     }
-    ws::StepArgs a{};
-    a.g = ws->g;
-    const double h2 = ws->h * ws->h;
-    a.c.c1 = (float)kW1;
-    a.c.c2 = (float)kW2;
-    a.c.c3 = (float)kW3;
-    a.c.c4 = (float)kW4;
-    a.gx = ws->gx;
-    a.gy = ws->gy;
-    a.gz = ws->gz;
-    a.traces = ws->traces;
-    a.nt_max = ws->nt_max;
-    a.status = ws->status;
-    a.src.n = (int)ws->src.size();
+    ws::StepArgs a = base_args(ws);
     for (int s = 0; s < nsteps; ++s) {
-        const double t = double(ws->step) * ws->dt;
-        for (int q = 0; q < a.src.n; ++q) {
-            const SourceDef &d = ws->src[q];
-            a.src.s[q] = ws::SourceSample{d.i, d.j, d.k, (float)(h2 * ricker(t, d.f0, d.t0, d.amp))};
-        }
-        a.trace_step = ws->step - ws->trace_start;
-        float *u = ws->buf[ws->cur];
-        float *up = ws->buf[1 - ws->cur];
-        cudaError_t e;
         if (ws->storage != WS_STORAGE_FP32) {
+            sources_of_step(ws, ws->step, &a.src);
+            a.trace_step = ws->step - ws->trace_start;
             double hint = 0.0;
             for (int q = 0; q < a.src.n; ++q)
                 hint = std::max(hint, std::fabs((double)a.src.s[q].amp) * ws->wmax);
-            e = ws::launch_step_stream16(ws->storage, &ws->t16_halo[ws->cur],
-                                         &ws->t16_tile[1 - ws->cur], &ws->t16_w, ws->buf16[1 - ws->cur],
-                                         a, ws->scale, ws->step, (float)hint, tiling,
-                                         ws->nrec > 0 ? ws->rec_ptr : nullptr, ws->rec_entries,
-                                         ws->stream);
+            cudaError_t e = ws::launch_step_stream16(
+                ws->storage, &ws->t16_halo[ws->cur], &ws->t16_tile[1 - ws->cur], &ws->t16_w,
+                ws->buf16[1 - ws->cur], a, ws->scale, ws->step, (float)hint, tiling,
+                ws->nrec > 0 ? ws->rec_ptr : nullptr, ws->rec_entries, ws->stream);
             ws->launches++;
-        } else if (kern == WS_KERNEL_STREAM) {
-            e = ws::launch_step_stream(&ws->tmap_halo[ws->cur], &ws->tmap_tile[1 - ws->cur],
-                                       &ws->tmap_w, up, a, tiling,
-                                       ws->nrec > 0 ? ws->rec_ptr : nullptr, ws->rec_entries,
-                                       ws->stream);
-            ws->launches++;
+            if (e != cudaSuccess) return cuda_fail(e, "ws_step launch");
         } else {
-            e = ws::launch_step_direct(u, up, ws->w, a, ws->stream);
-            ws->launches++;
-            if (e == cudaSuccess && ws->nrec > 0) {
-                e = ws::launch_gather_receivers(up, ws->rec_pidx, ws->nrec, ws->traces, ws->nt_max,
-                                                a.trace_step, ws->stream);
-                ws->launches++;
-            }
+            const int c = ws->cur;
+            int rc = step_fp32(ws, a, kern, tiling, ws->buf[c], &ws->tmap_halo[c], ws->buf[1 - c],
+                               &ws->tmap_tile[1 - c], ws->buf[1 - c], ws->step, true,
+                               ws->nrec > 0);
+            if (rc != WS_OK) return rc;
         }
-        if (e != cudaSuccess) return cuda_fail(e, "ws_step launch");
         ws->cur = 1 - ws->cur;
         ws->step++;
     }
@@ -758,6 +862,152 @@ int ws_energy_noalloc(const float *u, const float *u_prev, const float *v, int n
     WS_CUDA(ws::launch_energy_noalloc(u, u_prev, v, nx, ny, nz, h, dt, c, e,
                                       static_cast<cudaStream_t>(cuda_stream)),
             "ws_energy_noalloc");
+    return WS_OK;
+}
+
+int ws_adjoint_gradient(ws_t ws, const float *data, int mode, float *grad_m, double *misfit,
+                        int on_device) {
+    if (!ws || !data || !grad_m) return fail(WS_ERR_BADARG, "ws_adjoint_gradient: NULL argument");
+    if (mode != WS_ADJ_DATA && mode != WS_ADJ_RESIDUAL)
+        return fail(WS_ERR_BADARG, "ws_adjoint_gradient: unknown mode %d", mode);
+    if (!ws->vel_ok) return fail(WS_ERR_STATE, "ws_adjoint_gradient: no valid velocity model");
+    if (ws->nrec == 0) return fail(WS_ERR_STATE, "ws_adjoint_gradient: no receivers");
+    if (ws->storage != WS_STORAGE_FP32)
+        return fail(WS_ERR_STATE, "ws_adjoint_gradient: needs FP32 field storage");
+    const ws::Geom &g = ws->g;
+    const int N = ws->nt_max;
+    const int C = (int)std::ceil(std::sqrt((double)N));    // states per segment
+    const int nck = (N + C - 1) / C;                        // segments
+    int kern = WS_KERNEL_STREAM;
+    ws::StreamTiling tiling{};
+    int rc = prepare_fp32(ws, &kern, &tiling);
+    if (rc != WS_OK) return rc;
+    const bool maps = kern == WS_KERNEL_STREAM;
+    const size_t fb = field_bytes(g);
+    const size_t ncell = size_t(g.nx) * g.ny * g.nz;
+    const size_t ntr = size_t(ws->nrec) * N;
+    const cudaStream_t st = ws->stream;
+    Scratch sc(st);
+
+    // checkpoints (u^{jC}, u^{jC-1}), j = 1 .. nck-1; segment states; rho
+    std::vector<float *> ck(2 * size_t(nck - 1), nullptr);
+    for (auto &c : ck) WS_CUDA(sc.alloc(&c, fb), "cudaMalloc checkpoint");
+    std::vector<MappedField> seg(C);
+    MappedField segprev, rho[2];
+    for (auto &f : seg)
+        if ((rc = alloc_field(ws, sc, &f, maps, true)) != WS_OK) return rc;
+    if ((rc = alloc_field(ws, sc, &segprev, maps, true)) != WS_OK) return rc;
+    for (auto &f : rho)
+        if ((rc = alloc_field(ws, sc, &f, maps, true)) != WS_OK) return rc;
+    double *acc = nullptr, *partials = nullptr;
+    float *r = nullptr, *grad = grad_m;
+    const float *d = data;
+    int *rec = nullptr;
+    const int np = ws::residual_partial_count();
+    WS_CUDA(sc.alloc(&acc, sizeof(double) * ncell), "cudaMalloc gradient accumulator");
+    WS_CUDA(sc.alloc(&partials, sizeof(double) * (np + 1)), "cudaMalloc misfit partials");
+    WS_CUDA(sc.alloc(&r, sizeof(float) * ntr), "cudaMalloc residual");
+    WS_CUDA(sc.alloc(&rec, sizeof(int) * 3 * ws->nrec), "cudaMalloc receivers");
+    WS_CUDA(cudaMemsetAsync(acc, 0, sizeof(double) * ncell, st), "zero gradient accumulator");
+    WS_CUDA(cudaMemcpyAsync(rec, ws->rec_ijk.data(), sizeof(int) * 3 * ws->nrec,
+                            cudaMemcpyHostToDevice, st),
+            "upload receivers");
+    if (!on_device) {
+        float *dd = nullptr;
+        WS_CUDA(sc.alloc(&dd, sizeof(float) * ntr), "cudaMalloc observed data");
+        WS_CUDA(cudaMemcpyAsync(dd, data, sizeof(float) * ntr, cudaMemcpyHostToDevice, st),
+                "upload observed data");
+        d = dd;
+        WS_CUDA(sc.alloc(&grad, sizeof(float) * ncell), "cudaMalloc gradient");
+    }
+
+    // 1. forward from rest, recording the traces and the checkpoints
+    for (int b = 0; b < 2; ++b) WS_CUDA(cudaMemsetAsync(ws->buf[b], 0, fb, st), "zero fields");
+    WS_CUDA(cudaMemsetAsync(ws->traces, 0, sizeof(float) * ntr, st), "zero traces");
+    ws->step = 0;
+    ws->trace_start = 0;
+    ws::StepArgs a = base_args(ws);
+    for (int n = 0; n < N; ++n) {
+        if (n > 0 && n % C == 0) {
+            const int j = n / C;
+            WS_CUDA(cudaMemcpyAsync(ck[2 * (j - 1)], ws->buf[ws->cur], fb, cudaMemcpyDeviceToDevice, st),
+                    "save checkpoint");
+            WS_CUDA(cudaMemcpyAsync(ck[2 * (j - 1) + 1], ws->buf[1 - ws->cur], fb,
+                                    cudaMemcpyDeviceToDevice, st),
+                    "save checkpoint");
+        }
+        const int c = ws->cur;
+        rc = step_fp32(ws, a, kern, tiling, ws->buf[c], &ws->tmap_halo[c], ws->buf[1 - c],
+                       &ws->tmap_tile[1 - c], ws->buf[1 - c], n, true, true);
+        if (rc != WS_OK) return rc;
+        ws->cur = 1 - c;
+        ws->step++;
+    }
+
+    // 2. residual and misfit
+    WS_CUDA(ws::launch_residual(mode == WS_ADJ_DATA ? ws->traces : d,
+                                mode == WS_ADJ_DATA ? d : nullptr, (long long)ntr, r, partials,
+                                partials + np, st),
+            "residual kernels");
+    ws->launches += 2;
+
+    // 3. backward: rho^k, k = N .. 1, segment by segment, the segment's
+    // states recomputed from its checkpoint
+    const ws::Coeffs cf{(float)kW1, (float)kW2, (float)kW3, (float)kW4};
+    int rc_cur = 0;   // rho[rc_cur] = rho^{k+1}, rho[1 - rc_cur] = rho^{k+2}
+    for (int j = nck - 1; j >= 0; --j) {
+        const int n0 = j * C, n1 = std::min(n0 + C, N);
+        if (j == 0) {
+            WS_CUDA(cudaMemsetAsync(seg[0].p, 0, fb, st), "zero initial state");
+            WS_CUDA(cudaMemsetAsync(segprev.p, 0, fb, st), "zero initial state");
+        } else {
+            WS_CUDA(cudaMemcpyAsync(seg[0].p, ck[2 * (j - 1)], fb, cudaMemcpyDeviceToDevice, st),
+                    "restore checkpoint");
+            WS_CUDA(cudaMemcpyAsync(segprev.p, ck[2 * (j - 1) + 1], fb, cudaMemcpyDeviceToDevice, st),
+                    "restore checkpoint");
+        }
+        for (int t = 0; t + 1 < n1 - n0; ++t) {
+            const MappedField &um = t == 0 ? segprev : seg[t - 1];
+            rc = step_fp32(ws, a, kern, tiling, seg[t].p, &seg[t].halo, um.p, &um.tile,
+                           seg[t + 1].p, n0 + t, true, false);
+            if (rc != WS_OK) return rc;
+        }
+        for (int k = n1; k > n0; --k) {
+            MappedField &r1 = rho[rc_cur], &r2 = rho[1 - rc_cur];
+            rc = step_fp32(ws, a, kern, tiling, r1.p, &r1.halo, r2.p, &r2.tile, r2.p, k, false,
+                           false);
+            if (rc != WS_OK) return rc;
+            rc_cur = 1 - rc_cur;   // rho[rc_cur] = rho^k
+            WS_CUDA(ws::launch_inject(rho[rc_cur].p, ws->w, ws->gx, ws->gy, ws->gz, g, rec,
+                                      ws->nrec, r, N, k - 1, st),
+                    "adjoint injection kernel");
+            ws::Sources src{};
+            sources_of_step(ws, k - 1, &src);
+            WS_CUDA(ws::launch_imaging(rho[rc_cur].p, seg[k - 1 - n0].p, g, cf, src, ws->gx, ws->gy,
+                                       ws->gz, acc, st),
+                    "gradient imaging kernel");
+            ws->launches += 2;
+        }
+    }
+    const double hdt = ws->h / ws->dt;
+    WS_CUDA(ws::launch_finalize_gradient(acc, ws->w, g, hdt * hdt, grad, st),
+            "gradient finalize kernel");
+    ws->launches++;
+    if (!on_device)
+        WS_CUDA(cudaMemcpyAsync(grad_m, grad, sizeof(float) * ncell, cudaMemcpyDeviceToHost, st),
+                "copy gradient");
+    double J = 0.0;
+    WS_CUDA(cudaMemcpyAsync(&J, partials + np, sizeof(double), cudaMemcpyDeviceToHost, st),
+            "copy misfit");
+    WS_CUDA(cudaStreamSynchronize(st), "ws_adjoint_gradient");
+    if (misfit) *misfit = J;
+    unsigned status = 0;
+    WS_CUDA(cudaMemcpy(&status, ws->status, sizeof status, cudaMemcpyDeviceToHost),
+            "ws_adjoint_gradient");
+    if (status & ws::kStatusTimeout) {
+        WS_CUDA(cudaMemset(ws->status, 0, sizeof(unsigned)), "ws_adjoint_gradient");
+        return fail(WS_ERR_TIMEOUT, "a bounded device wait ran out in a step kernel");
+    }
     return WS_OK;
 }
 

@@ -95,14 +95,18 @@ struct StepArgs {
 };
 
 // Launchers (stream-ordered, no synchronization).
-cudaError_t launch_step_direct(const float *u, float *up, const float *w, const StepArgs &a,
-                               cudaStream_t s);
+// out = u^{n+1} from u = u^n and up = u^{n-1}; out may be up (in place).
+cudaError_t launch_step_direct(const float *u, const float *up, float *out, const float *w,
+                               const StepArgs &a, cudaStream_t s);
 cudaError_t launch_gather_receivers(const float *u_next, const long long *rec_pidx, int nrec,
                                     float *traces, int nt_max, long long trace_step,
                                     cudaStream_t s);
 cudaError_t launch_velocity_to_w(float *w, const Geom &g, double dt_over_h,
                                  unsigned *extrema /* [2]: max bits, min bits */,
                                  cudaStream_t s);
+cudaError_t launch_slowness2_to_w(float *w, const Geom &g, double dt_over_h2,
+                                  unsigned *extrema /* [2]: max m bits, min m bits */,
+                                  cudaStream_t s);
 
 struct StreamTiling {
     int tx, ty, zb;
@@ -138,6 +142,25 @@ cudaError_t launch_encode16(int storage, const float *f, uint16_t *out, const Ge
                             int slot, cudaStream_t s);
 cudaError_t launch_decode16(int storage, const uint16_t *in, float *f, const Geom &g,
                             const Scale16 *sc, int slot, cudaStream_t s);
+
+// ---- adjoint gradient ----
+int residual_partial_count();
+// r = traces - d_obs (n values; r = traces when d_obs is null),
+// *misfit = sum r^2 / 2 (FP64, fixed order);
+// partials holds residual_partial_count() doubles.
+cudaError_t launch_residual(const float *traces, const float *d_obs, long long n, float *r,
+                            double *partials, double *misfit, cudaStream_t s);
+// rho[rec] += W G r[:, col] at every receiver (rec_ijk: [nrec][3] device).
+cudaError_t launch_inject(float *rho, const float *w, const float *gx, const float *gy,
+                          const float *gz, const Geom &g, const int *rec_ijk, int nrec,
+                          const float *r, int nt, int col, cudaStream_t s);
+// acc (unpadded FP64) += rho * L u, plus rho * amp / G at source cells.
+cudaError_t launch_imaging(const float *rho, const float *u, const Geom &g, const Coeffs &c,
+                           const Sources &src, const float *gx, const float *gy, const float *gz,
+                           double *acc, cudaStream_t s);
+// grad (unpadded float) = -V^2 acc, V^2 = W (h / dt)^2.
+cudaError_t launch_finalize_gradient(const double *acc, const float *w, const Geom &g,
+                                     double h_over_dt2, float *grad, cudaStream_t s);
 
 // Discrete energy (FP64): partial sums per (row block, plane) into
 // partials[energy_partial_count(ny, nz)], then their fixed-order sum into *out.

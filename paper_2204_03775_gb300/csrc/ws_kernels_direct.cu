@@ -13,7 +13,7 @@ namespace ws {
 // u: u^n, up: u^{n-1} on entry and u^{n+1} on exit (same cell only),
 // w: (V dt / h)^2.
 __global__ void __launch_bounds__(256) step_direct_kernel(const float *__restrict__ u,
-                                                          float *__restrict__ up,
+                                                          const float *up, float *out,
                                                           const float *__restrict__ w,
                                                           const __grid_constant__ StepArgs a) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -47,14 +47,14 @@ __global__ void __launch_bounds__(256) step_direct_kernel(const float *__restric
         const SourceSample &ss = a.src.s[q];
         if (ss.i == i && ss.j == j && ss.k == k) un = fmaf(wc, ss.amp, un);
     }
-    up[p] = un;
+    out[p] = un;
 }
 
-cudaError_t launch_step_direct(const float *u, float *up, const float *w, const StepArgs &a,
-                               cudaStream_t s) {
+cudaError_t launch_step_direct(const float *u, const float *up, float *out, const float *w,
+                               const StepArgs &a, cudaStream_t s) {
     dim3 block(32, 8, 1);
     dim3 grid((a.g.nx + 31) / 32, (a.g.ny + 7) / 8, a.g.nz);
-    step_direct_kernel<<<grid, block, 0, s>>>(u, up, w, a);
+    step_direct_kernel<<<grid, block, 0, s>>>(u, up, out, w, a);
     return cudaGetLastError();
 }
 
@@ -109,6 +109,46 @@ __global__ void velocity_to_w_kernel(float *__restrict__ w, Geom g, double dt_ov
         atomicMax(&extrema[0], vmax);
         atomicMin(&extrema[1], vmin);
     }
+}
+
+// In place: m (squared slowness, s^2/m^2) -> (V dt / h)^2 = (dt / h)^2 / m,
+// in double, rounded once. extrema[0] / extrema[1] collect max(m) / min(m)
+// as float bits; a value that is not finite and > 0 contributes 0 to the
+// minimum, which the host rejects.
+__global__ void slowness2_to_w_kernel(float *__restrict__ w, Geom g, double dt_over_h2,
+                                      unsigned *__restrict__ extrema) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y;
+    const int k = blockIdx.z;
+    unsigned mmax = 0u, mmin = 0x7f800000u;
+    if (i < g.nx) {
+        const long long p = pidx(g, i, j, k);
+        const float m = w[p];
+        if (m > 0.0f && isfinite(m)) {
+            mmax = __float_as_uint(m);
+            mmin = mmax;
+        } else {
+            mmin = 0u;
+        }
+        w[p] = (float)(dt_over_h2 / (double)m);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        mmax = max(mmax, __shfl_xor_sync(0xffffffffu, mmax, o));
+        mmin = min(mmin, __shfl_xor_sync(0xffffffffu, mmin, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(&extrema[0], mmax);
+        atomicMin(&extrema[1], mmin);
+    }
+}
+
+cudaError_t launch_slowness2_to_w(float *w, const Geom &g, double dt_over_h2, unsigned *extrema,
+                                  cudaStream_t s) {
+    dim3 block(128, 1, 1);
+    dim3 grid((g.nx + 127) / 128, g.ny, g.nz);
+    slowness2_to_w_kernel<<<grid, block, 0, s>>>(w, g, dt_over_h2, extrema);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_velocity_to_w(float *w, const Geom &g, double dt_over_h, unsigned *extrema,
