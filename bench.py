@@ -49,6 +49,10 @@ def parse_args():
     ap.add_argument("--zblock", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the 64-shot batched-launch report")
+    ap.add_argument("--no-adjoint", action="store_true",
+                    help="skip the 256^3 16-shot adjoint-gradient report")
     ap.add_argument("--no-storage16", action="store_true",
                     help="skip the BF16/FP16 storage timings and errors")
     return ap.parse_args()
@@ -233,6 +237,152 @@ def storage16_report(w, K, W, stream, peak):
     return out
 
 
+def _shot_handle(wsb, w, nt_max):
+    h = wsb.ws_create(w.nx, w.ny, w.nz, w.h, w.dt)
+    wsb.ws_set_velocity(h, w.vel)
+    wsb.ws_set_sponge(h, *w.sponge)
+    for s in w.sources:
+        wsb.ws_add_source(h, *s)
+    wsb.ws_set_receivers(h, w.receivers, nt_max)
+    return h
+
+
+def batched_report(peak):
+    """64 shots on uneven grids (96^3 .. 320x320x256), 500 steps each: one
+    persistent launch per step over all shots, replayed as a CUDA graph, with
+    the tiling the batch's online tuner chose; against the same shots stepped
+    one after another with ws_step (per-shot launches, default tiling)."""
+    import torch
+    import paper_2204_03775_gb300 as wsb
+    from paper_2204_03775_gb300 import synthetic
+
+    shots = synthetic.batched_shots()
+    nt = shots[0].nt
+    cells = sum(w.points for w in shots)
+    hs = [_shot_handle(wsb, w, nt) for w in shots]
+    b = wsb.ws_batch_create(hs)
+
+    def restart():
+        for h, w in zip(hs, shots):
+            wsb.ws_write_field(h, None, None, 0)
+            wsb.ws_set_receivers(h, w.receivers, nt)
+
+    t0 = time.perf_counter()
+    wsb.ws_batch_step(b, 60)            # online tuning: 25 candidates x 2 steps, then the best
+    wsb.ws_batch_synchronize(b)
+    tune_s = time.perf_counter() - t0
+    tiling = wsb.ws_batch_get_tiling(b)
+    wsb.ws_batch_set_tiling(b, *tiling)
+    restart()
+    wsb.ws_batch_step(b, nt)            # captures the graph of nt launches
+    wsb.ws_batch_synchronize(b)
+    restart()
+    torch.cuda.synchronize()
+    l0 = wsb.ws_batch_launch_count(b)
+    t0 = time.perf_counter()
+    wsb.ws_batch_step(b, nt)
+    wsb.ws_batch_synchronize(b)
+    batch_s = time.perf_counter() - t0
+    launches = wsb.ws_batch_launch_count(b) - l0
+    restart()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for h in hs:
+        wsb.ws_step(h, nt)
+    torch.cuda.synchronize()
+    seq_s = time.perf_counter() - t0
+    for h in hs:
+        wsb.ws_synchronize(h)
+    wsb.ws_batch_destroy(b)
+    for h in hs:
+        wsb.ws_destroy(h)
+    rate = cells * nt / batch_s / 1e9
+    return {"workload": f"{len(shots)} shots on grids from the seed, sizes in [96,320]x[96,320]x"
+                        f"[96,256] ({cells / 1e6:.0f} M cells), {nt} steps each, FP32",
+            "value": rate, "unit": UNIT, "ms_per_step": 1e3 * batch_s / nt,
+            "launches": launches, "graph": True,
+            "tiling": {"tile": f"{tiling[0]}x{tiling[1]}", "zmul": tiling[2],
+                       "tuning_s": tune_s},
+            "roofline_frac": BYTES_PER_POINT * rate / peak,
+            "sequential": {"value": cells * nt / seq_s / 1e9, "unit": UNIT,
+                           "what": "the same shots one after another, ws_step each"},
+            "timing": "host clock around ws_batch_step + ws_batch_synchronize"}
+
+
+def adjoint_report():
+    """Gradient of the L2 trace misfit w.r.t. squared slowness on the 256^3
+    survey: 16 shots, 128 x 128 receivers, 800 steps, sqrt(N) checkpoints;
+    time per 16-shot gradient against one 16-shot forward modelling."""
+    import numpy as np
+    import torch
+    import paper_2204_03775_gb300 as wsb
+    from paper_2204_03775_gb300 import synthetic
+
+    w = synthetic.adjoint_survey()
+    dev = torch.device("cuda")
+    m_true = torch.from_numpy((1.0 / w.vel_true.astype(np.float64) ** 2).astype(np.float32)).to(dev)
+    m0 = torch.from_numpy((1.0 / w.vel_start.astype(np.float64) ** 2).astype(np.float32)).to(dev)
+    hs = []
+    for shot in w.shots:
+        h = wsb.ws_create(w.nx, w.ny, w.nz, w.h, w.dt)
+        wsb.ws_set_sponge(h, *w.sponge)
+        for s in shot:
+            wsb.ws_add_source(h, *s)
+        wsb.ws_set_receivers(h, w.receivers, w.nt)
+        hs.append(h)
+    for h in hs:
+        wsb.ws_set_slowness2(h, m0)
+        tiling = wsb.ws_autotune(h)     # timed once, then cached for the grid size
+    nrec = len(w.receivers)
+
+    def forward(m):
+        out = []
+        for h in hs:
+            wsb.ws_set_slowness2(h, m)
+            wsb.ws_write_field(h, None, None, 0)
+            wsb.ws_set_receivers(h, w.receivers, w.nt)
+            wsb.ws_step(h, w.nt)
+            t = torch.empty((nrec, w.nt), dtype=torch.float32, device=dev)
+            wsb.ws_read_traces(h, t)
+            out.append(t)
+        torch.cuda.synchronize()
+        return out
+
+    d_obs = forward(m_true)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    forward(m0)
+    fwd_s = time.perf_counter() - t0
+    g = torch.zeros_like(m0)
+    gs = torch.empty_like(m0)
+    times = []
+    for rep in range(2):
+        g.zero_()
+        J = 0.0
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for h, d in zip(hs, d_obs):
+            wsb.ws_set_slowness2(h, m0)
+            _, j = wsb.ws_adjoint_gradient(h, d, wsb.WS_ADJ_DATA, gs)
+            g += gs
+            J += j
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+    for h in hs:
+        wsb.ws_destroy(h)
+    cells = w.nx * w.ny * w.nz
+    return {"workload": f"adjoint_survey {w.nx}^3, 16 shots, {nrec} receivers, {w.nt} steps, "
+                        "true = layered + 10% Gaussian blob, start = layered",
+            "gradient_s": min(times), "forward_s": fwd_s,
+            "gradient_over_forward": min(times) / fwd_s,
+            "forward_rate": {"value": len(hs) * cells * w.nt / fwd_s / 1e9, "unit": UNIT},
+            "misfit": J, "grad_max_abs": float(g.abs().max()),
+            "tiling": {"tile": f"{tiling[0]}x{tiling[1]}", "zblock": tiling[2]},
+            "passes": "forward (traces + sqrt(N) checkpoints), residual, then per segment a "
+                      "recomputation and the adjoint steps with injection and imaging",
+            "timing": "host clock, 16 shots one after another"}
+
+
 def run_reference(args):
     """The oracle as it stands, timed on the host cores (rank 0 only)."""
     world, rank, _ = dist_setup(args.gpus)
@@ -395,6 +545,10 @@ def main():
     wsb.ws_destroy(h)
     if world == 1 and not args.no_storage16 and n >= 64:
         line["storage16"] = storage16_report(w, K, W, stream, peak)
+    if world == 1 and not args.no_batched:
+        line["batched"] = batched_report(peak)
+    if world == 1 and not args.no_adjoint:
+        line["adjoint"] = adjoint_report()
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w)
     print(json.dumps(line), flush=True)

@@ -239,6 +239,63 @@ int ws_set_storage(ws_t ws, int storage);
  * else BADARG. */
 int ws_set_kernel(ws_t ws, int kernel, int tile_x, int tile_y, int zblock);
 
+/* Pick the streaming kernel's tile and z-block for this handle's grid by
+ * timing the candidates (every tile that fits; z-blocks giving the default
+ * length and about 1, 2, 4 and 8 x the resident CTAs in work items) on
+ * steps written to a scratch field, so the state is unchanged; then select
+ * WS_KERNEL_STREAM with the fastest (WS_KERNEL_DIRECT if no tile fits).
+ * Results are cached per grid size for the process. Outputs may be NULL.
+ * Needs a velocity model and FP32 storage, else STATE. Synchronizes. */
+int ws_autotune(ws_t ws, int *tile_x, int *tile_y, int *zblock);
+
+/* ---- batched shots -------------------------------------------------------
+ * A batch advances several independent handles ("shots": each its own grid
+ * size, model, taper, sources and receivers) together: every step is ONE
+ * persistent launch of the streaming kernel over the work items of all
+ * shots, and each ws_batch_step(n) replays a CUDA graph of n such launches.
+ * The results are bit for bit those of ws_step on each handle (the same
+ * arithmetic per cell, whatever the tiling). The paper's many-problem use is
+ * one large grid per wafer (Section IV); batching many smaller grids per
+ * GPU is this library's addition.
+ *
+ * The batch references the handles (it does not own them; destroy the batch
+ * first). Every shot must have nx >= 32 and ny >= 8. Work runs on a stream
+ * the batch creates, ordered after each shot's pending work on its own
+ * stream, and each shot's later work on its own stream is ordered after it.
+ *
+ * Tiling: unless fixed with ws_batch_set_tiling, ws_batch_step tunes online:
+ * while candidates remain untried, steps are taken two at a time with the
+ * next candidate (tile x z-block rule), the second step timed; then the
+ * fastest is kept. Tuning changes timing only, never results. */
+typedef struct ws_batch *ws_batch_t;
+
+/* Create a batch of nshots distinct handles. Errors: BADARG (NULL or
+ * repeated handle, a shot smaller than every tile), OOM, CUDA. */
+int ws_batch_create(ws_batch_t *out, int nshots, const ws_t *shots);
+
+/* Free the batch (its stream, graphs and tables; not the handles). */
+int ws_batch_destroy(ws_batch_t b);
+
+/* Fix the tile (tile_x x tile_y, as in ws_set_kernel) and the z-block rule:
+ * zmul = 0 gives each shot its default z-block, zmul >= 1 z-blocks that
+ * make about zmul x (resident CTAs) items over the batch, shared among the
+ * shots by their sizes. (0, 0, any) returns to online tuning. */
+int ws_batch_set_tiling(ws_batch_t b, int tile_x, int tile_y, int zmul);
+
+/* The tiling in use (all zero before the first step). */
+int ws_batch_get_tiling(ws_batch_t b, int *tile_x, int *tile_y, int *zmul);
+
+/* Advance every shot nsteps steps (asynchronous). Each shot needs a velocity
+ * model, FP32 storage and room in its receiver buffer, else STATE. */
+int ws_batch_step(ws_batch_t b, int nsteps);
+
+/* Wait for the batch's stream; report (and clear) a bounded-wait timeout
+ * recorded by a batched step (TIMEOUT). */
+int ws_batch_synchronize(ws_batch_t b);
+
+/* Kernel launches issued by the batch (one per step). */
+long long ws_batch_launch_count(ws_batch_t b);
+
 /* Wait for the stream, then report a device-side failure recorded since the
  * last call (TIMEOUT when a bounded wait in a kernel ran out). Clears it. */
 int ws_synchronize(ws_t ws);

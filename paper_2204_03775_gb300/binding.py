@@ -87,6 +87,14 @@ def load_library(build_if_missing: bool = False):
         "ws_energy": (i, [vp, ctypes.POINTER(d)]),
         "ws_energy_noalloc": (i, [vp, vp, vp, i, i, i, d, d, vp, vp]),
         "ws_last_error": (ctypes.c_char_p, []),
+        "ws_autotune": (i, [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]),
+        "ws_batch_create": (i, [ctypes.POINTER(vp), i, vp]),
+        "ws_batch_destroy": (i, [vp]),
+        "ws_batch_set_tiling": (i, [vp, i, i, i]),
+        "ws_batch_get_tiling": (i, [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]),
+        "ws_batch_step": (i, [vp, i]),
+        "ws_batch_synchronize": (i, [vp]),
+        "ws_batch_launch_count": (ll, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -288,6 +296,66 @@ def ws_energy_noalloc(u, u_prev, v, h: float, dt: float, out, stream=None) -> No
         ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(u_prev.data_ptr()),
         ctypes.c_void_p(v.data_ptr()), nx, ny, nz, float(h), float(dt),
         ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(raw or None)), "ws_energy_noalloc")
+
+
+def ws_autotune(ws: Handle):
+    """Time the streaming kernel's tilings on this grid; returns (tile_x, tile_y, zblock)."""
+    tx, ty, zb = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(load_library().ws_autotune(ws.ptr, ctypes.byref(tx), ctypes.byref(ty), ctypes.byref(zb)),
+           "ws_autotune")
+    return tx.value, ty.value, zb.value
+
+
+class Batch:
+    """Owned ws_batch_t; keeps its shot handles alive; destroyed before them."""
+
+    def __init__(self, ptr: int, shots):
+        self.ptr = ctypes.c_void_p(ptr)
+        self.shots = list(shots)
+
+    def __del__(self):
+        if self.ptr and _lib is not None:
+            _lib.ws_batch_destroy(self.ptr)
+            self.ptr = ctypes.c_void_p(None)
+
+
+def ws_batch_create(shots) -> Batch:
+    shots = list(shots)
+    arr = (ctypes.c_void_p * len(shots))(*[h.ptr.value for h in shots])
+    out = ctypes.c_void_p()
+    _check(load_library().ws_batch_create(ctypes.byref(out), len(shots),
+                                          ctypes.cast(arr, ctypes.c_void_p)), "ws_batch_create")
+    return Batch(out.value, shots)
+
+
+def ws_batch_destroy(b: Batch) -> None:
+    if b.ptr:
+        _check(load_library().ws_batch_destroy(b.ptr), "ws_batch_destroy")
+        b.ptr = ctypes.c_void_p(None)
+
+
+def ws_batch_set_tiling(b: Batch, tile_x: int, tile_y: int, zmul: int = 0) -> None:
+    _check(load_library().ws_batch_set_tiling(b.ptr, int(tile_x), int(tile_y), int(zmul)),
+           "ws_batch_set_tiling")
+
+
+def ws_batch_get_tiling(b: Batch):
+    tx, ty, zm = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(load_library().ws_batch_get_tiling(b.ptr, ctypes.byref(tx), ctypes.byref(ty),
+                                              ctypes.byref(zm)), "ws_batch_get_tiling")
+    return tx.value, ty.value, zm.value
+
+
+def ws_batch_step(b: Batch, nsteps: int) -> None:
+    _check(load_library().ws_batch_step(b.ptr, int(nsteps)), "ws_batch_step")
+
+
+def ws_batch_synchronize(b: Batch) -> None:
+    _check(load_library().ws_batch_synchronize(b.ptr), "ws_batch_synchronize")
+
+
+def ws_batch_launch_count(b: Batch) -> int:
+    return int(load_library().ws_batch_launch_count(b.ptr))
 
 
 def ws_launch_count(ws: Handle) -> int:

@@ -73,9 +73,10 @@ __host__ __device__ inline long long pidx(const Geom &g, int i, int j, int k) {
     return ((long long)(k + kHalo) * g.pny + (j + kHalo)) * g.pnx + (i + kXOff);
 }
 
-// Receivers grouped for the streaming kernel: per xy tile a contiguous range
-// of entries sorted by k. owner = thread index inside the tile's CTA,
-// lane = which of the thread's 4 x-cells, slot = receiver number r.
+// Receivers grouped for the streaming kernels: per (xy tile, consumer warp)
+// a contiguous range of entries sorted by k, ranges indexed
+// tile * warps + warp. owner = thread index inside the tile's CTA (in that
+// warp), lane = which of the thread's 4 x-cells, r = receiver number.
 struct RecEntry {
     int k;
     int owner;
@@ -118,6 +119,34 @@ cudaError_t launch_step_stream(const CUtensorMap *tmap_u, const CUtensorMap *tma
                                const CUtensorMap *tmap_w, float *up, const StepArgs &a,
                                const StreamTiling &t, const int *rec_ptr, const RecEntry *rec,
                                cudaStream_t s);
+
+// One shot of a batched step (global memory, written by the host before the
+// launch). Step t of a run reads u^n from buf[cur0 ^ (t & 1)] with
+// halo[cur0 ^ (t & 1)], u^{n-1} with tile[the other], writes u^{n+1} over
+// u^{n-1}; src holds nsrc samples per step of the run ([t][nsrc]); trace
+// column of step t = trace_col0 + t (traces null: no receivers).
+struct alignas(128) BatchShot {
+    CUtensorMap halo[2], tile[2], w;
+    float *buf[2];
+    const float *gx, *gy, *gz;
+    const SourceSample *src;
+    float *traces;
+    const int *rec_ptr;
+    const RecEntry *rec;
+    Geom g;
+    long long trace_col0;
+    int nsrc, nt_max, cur0, zb, tiles_x, ntiles;
+};
+
+// SMs x resident CTAs of the streaming kernel (batch: the batched one) with
+// tile tx x ty. Also sets the kernel's shared-memory limit, so call it once
+// before capturing launches into a graph.
+cudaError_t stream_slots(int tx, int ty, bool batch, int *slots);
+
+// One persistent launch over items[0..nitems) = (shot, item of the shot),
+// every shot with the tile tx x ty (stream_tiling_supported).
+cudaError_t launch_step_batch(const BatchShot *shots, const int2 *items, int nitems, int t,
+                              const Coeffs &c, unsigned *status, int tx, int ty, cudaStream_t s);
 
 // ---- 16-bit field storage (WS_STORAGE_BF16 / WS_STORAGE_FP16) ----
 // Ring of per-field power-of-two exponents and maxima, indexed by step & 3:

@@ -31,6 +31,12 @@
 // Every wait is bounded (kWaitLimitNs); on a timeout the kernel records
 // kStatusTimeout, all warps leave their loops, and the CTA waits (bounded)
 // for its copies in flight before it exits.
+//
+// The same pipeline serves two sources of work items: one grid whose maps
+// and arguments are kernel parameters (OneGrid), and a batch of independent
+// shots on grids of different sizes (ShotBatch), whose per-shot tensor maps,
+// geometry, sources and receivers sit in a descriptor table in global memory
+// and whose items from every shot share one persistent launch.
 #include <climits>
 
 #include "ws_ptx.cuh"
@@ -71,6 +77,93 @@ struct StreamMaps {
     CUtensorMap u, up, w;
 };
 
+// What the producer needs of an item: its extent and the three maps.
+struct Job {
+    Item it;
+    const CUtensorMap *u, *up, *w;
+};
+
+// What the consumers need of an item's grid.
+struct View {
+    Geom g;
+    const float *gx, *gy, *gz;
+    const SourceSample *src;   // this step's source samples
+    int nsrc;
+    float *traces;             // [nrec][nt_max]
+    int nt_max;
+    long long trace_step;
+    float *out;                // u^{n+1} field (padded)
+    const int *rec_ptr;        // per-tile receiver ranges, or null
+    const RecEntry *rec;
+};
+
+// Items of one grid; everything comes from kernel parameters.
+template <int TX, int TY>
+struct OneGrid {
+    const StreamMaps &mp;
+    const StepArgs &a;
+    float *up;
+    int zb, tiles_x, ntiles, n;
+    const int *rec_ptr;
+    const RecEntry *rec;
+
+    __device__ __forceinline__ int nitems() const { return n; }
+    __device__ __forceinline__ Job job(int item) const {
+        return Job{item_of(item, tiles_x, ntiles, zb, a.g.nz, TX, TY), &mp.u, &mp.up, &mp.w};
+    }
+    __device__ __forceinline__ Item view(int item, View *v) const {
+        v->g = a.g;
+        v->gx = a.gx;
+        v->gy = a.gy;
+        v->gz = a.gz;
+        v->src = a.src.s;
+        v->nsrc = a.src.n;
+        v->traces = a.traces;
+        v->nt_max = a.nt_max;
+        v->trace_step = a.trace_step;
+        v->out = up;
+        v->rec_ptr = rec_ptr;
+        v->rec = rec;
+        return item_of(item, tiles_x, ntiles, zb, a.g.nz, TX, TY);
+    }
+};
+
+// Items of a batch of shots: items[q] = (shot, item of that shot), step t of
+// the run; shot s reads u^n from buf[cur0 ^ (t & 1)].
+template <int TX, int TY>
+struct ShotBatch {
+    const BatchShot *shots;
+    const int2 *items;
+    int n, t;
+
+    __device__ __forceinline__ int nitems() const { return n; }
+    __device__ __forceinline__ Job job(int item) const {
+        const int2 e = items[item];
+        const BatchShot &s = shots[e.x];
+        const int p = s.cur0 ^ (t & 1);
+        return Job{item_of(e.y, s.tiles_x, s.ntiles, s.zb, s.g.nz, TX, TY), &s.halo[p],
+                   &s.tile[1 - p], &s.w};
+    }
+    __device__ __forceinline__ Item view(int item, View *v) const {
+        const int2 e = items[item];
+        const BatchShot &s = shots[e.x];
+        const int p = s.cur0 ^ (t & 1);
+        v->g = s.g;
+        v->gx = s.gx;
+        v->gy = s.gy;
+        v->gz = s.gz;
+        v->nsrc = s.nsrc;
+        v->src = s.src + (long long)t * s.nsrc;
+        v->traces = s.traces;
+        v->nt_max = s.nt_max;
+        v->trace_step = s.trace_col0 + t;
+        v->out = s.buf[1 - p];
+        v->rec_ptr = s.rec_ptr;
+        v->rec = s.rec;
+        return item_of(e.y, s.tiles_x, s.ntiles, s.zb, s.g.nz, TX, TY);
+    }
+};
+
 // Per-thread state of a consumer thread's walk down one item.
 struct Walk {
     float4 q[9];            // u^n of planes k-4 .. k+4 (rotated: see plane_step)
@@ -95,49 +188,47 @@ struct Kern {
     // its halo) into the g-th ring-A slot use, once its previous plane is
     // released. The box corner is interior (i0 - 4, j0 - 4), padded
     // (i0 + kXOff - 4, j0, z0 + pr); x is a multiple of 4 elements.
-    static __device__ __forceinline__ bool produce_a(R &rg, float *ringA, const StreamMaps &mp,
-                                                     unsigned g, const Item &it, int pr,
-                                                     unsigned *status) {
+    static __device__ __forceinline__ bool produce_a(R &rg, float *ringA, const Job &jb, unsigned g,
+                                                     int pr, unsigned *status) {
         const int slot = g & (NA - 1);
         if (!wait_phase(&rg.emptyA[slot], ((g / NA) & 1u) ^ 1u, &rg.abort, status)) return false;
         rg.issuedA[slot]++;
         mbar_arrive_expect_tx(&rg.fullA[slot], Cfg::kSlotABytes);
-        tma_load_3d(ringA + slot * Cfg::kSlotA, &mp.u, &rg.fullA[slot], it.i0 + kXOff - kHalo,
-                    it.j0, it.z0 + pr);
+        tma_load_3d(ringA + slot * Cfg::kSlotA, jb.u, &rg.fullA[slot], jb.it.i0 + kXOff - kHalo,
+                    jb.it.j0, jb.it.z0 + pr);
         return true;
     }
 
     // u^{n-1} and (V dt/h)^2 of interior plane z0 + b into the g-th ring-B use.
-    static __device__ __forceinline__ bool produce_b(R &rg, float *ringB, const StreamMaps &mp,
-                                                     unsigned g, const Item &it, int b,
-                                                     unsigned *status) {
+    static __device__ __forceinline__ bool produce_b(R &rg, float *ringB, const Job &jb, unsigned g,
+                                                     int b, unsigned *status) {
         const int slot = g & (NB - 1);
         if (!wait_phase(&rg.emptyB[slot], ((g / NB) & 1u) ^ 1u, &rg.abort, status)) return false;
         rg.issuedB[slot]++;
         float *dst = ringB + slot * (2 * Cfg::kTile);
         mbar_arrive_expect_tx(&rg.fullB[slot], Cfg::kSlotBBytes);
-        tma_load_3d(dst, &mp.up, &rg.fullB[slot], it.i0 + kXOff, it.j0 + kHalo, it.z0 + b + kHalo);
-        tma_load_3d(dst + Cfg::kTile, &mp.w, &rg.fullB[slot], it.i0 + kXOff, it.j0 + kHalo,
-                    it.z0 + b + kHalo);
+        tma_load_3d(dst, jb.up, &rg.fullB[slot], jb.it.i0 + kXOff, jb.it.j0 + kHalo,
+                    jb.it.z0 + b + kHalo);
+        tma_load_3d(dst + Cfg::kTile, jb.w, &rg.fullB[slot], jb.it.i0 + kXOff, jb.it.j0 + kHalo,
+                    jb.it.z0 + b + kHalo);
         return true;
     }
 
     // One lane issues every copy of every item of this CTA, in the order the
     // consumers need them: the 8 planes of the queue prologue, then for each
     // plane k of the block its u^{n-1} / (V dt/h)^2 and the u^n plane k + 8.
-    static __device__ void producer(R &rg, float *ringA, float *ringB, const StreamMaps &mp,
-                                    const StepArgs &a, int zb, int tiles_x, int ntiles,
-                                    int nitems) {
+    template <class S>
+    static __device__ void producer(R &rg, float *ringA, float *ringB, const S &src,
+                                    unsigned *status) {
         unsigned gA = 0, gB = 0;
-        for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
-            const Item it = item_of(item, tiles_x, ntiles, zb, a.g.nz, TX, TY);
-            const int nb = it.z1 - it.z0, nplanes = nb + 2 * kHalo;
+        for (int item = blockIdx.x; item < src.nitems(); item += gridDim.x) {
+            const Job jb = src.job(item);
+            const int nb = jb.it.z1 - jb.it.z0, nplanes = nb + 2 * kHalo;
             for (int pr = 0; pr < 2 * kHalo; ++pr)
-                if (!produce_a(rg, ringA, mp, gA++, it, pr, a.status)) return;
+                if (!produce_a(rg, ringA, jb, gA++, pr, status)) return;
             for (int b = 0; b < nb; ++b) {
-                if (!produce_b(rg, ringB, mp, gB++, it, b, a.status)) return;
-                if (b + 2 * kHalo < nplanes &&
-                    !produce_a(rg, ringA, mp, gA++, it, b + 2 * kHalo, a.status))
+                if (!produce_b(rg, ringB, jb, gB++, b, status)) return;
+                if (b + 2 * kHalo < nplanes && !produce_a(rg, ringA, jb, gA++, b + 2 * kHalo, status))
                     return;
             }
         }
@@ -156,26 +247,27 @@ struct Kern {
     // compile time.
     template <int RQ>
     static __device__ __forceinline__ void plane_step(Walk &wk, R &rg, const float *ringA,
-                                                      const float *ringB, const StepArgs &a,
+                                                      const float *ringB, const View &v,
+                                                      const Coeffs &c, unsigned *status,
                                                       const Item &it, int k, int i, int j,
-                                                      int offA, int offB, const RecEntry *rec) {
+                                                      int offA, int offB) {
 #define QI(m) ((RQ + (m)) % 9)
 #define BI(d) ((RQ + (d)) % 3)
         // u^n of plane k + 4 into the queue
-        const float *sa = wait_a(wk, rg, ringA, wk.gAw, a.status);
+        const float *sa = wait_a(wk, rg, ringA, wk.gAw, status);
         wk.q[QI(8)] = lds4(sa + offA);
         ++wk.gAw;
 
         // u^{n-1} and (V dt/h)^2 of plane k
         const int sb = wk.gB & (NB - 1);
-        wk.ok = wk.ok && wait_phase(&rg.fullB[sb], (wk.gB / NB) & 1u, &rg.abort, a.status);
+        wk.ok = wk.ok && wait_phase(&rg.fullB[sb], (wk.gB / NB) & 1u, &rg.abort, status);
         const float *tb = ringB + sb * (2 * Cfg::kTile) + offB;
         const float4 upc = lds4(tb);
         const float4 wc = lds4(tb + Cfg::kTile);
         warp_arrive(&rg.emptyB[sb]);
         ++wk.gB;
 
-        if (k + 2 < it.z1) wk.gzb[BI(2)] = __ldg(a.gz + k + 2);
+        if (k + 2 < it.z1) wk.gzb[BI(2)] = __ldg(v.gz + k + 2);
 
         // u^n of plane k with its halo (waited for four planes ago)
         const float *row = ringA + (wk.gAr & (NA - 1)) * Cfg::kSlotA + offA;
@@ -222,10 +314,10 @@ struct Kern {
             }
             const float2 uc = pair(xc, p);
             // sum_m c_m (s_m - 6 u): exactly zero on constants (see Coeffs)
-            float2 lap = mul2(splat(a.c.c4), fma2(splat(-6.0f), uc, s[4]));
-            lap = fma2(splat(a.c.c3), fma2(splat(-6.0f), uc, s[3]), lap);
-            lap = fma2(splat(a.c.c2), fma2(splat(-6.0f), uc, s[2]), lap);
-            lap = fma2(splat(a.c.c1), fma2(splat(-6.0f), uc, s[1]), lap);
+            float2 lap = mul2(splat(c.c4), fma2(splat(-6.0f), uc, s[4]));
+            lap = fma2(splat(c.c3), fma2(splat(-6.0f), uc, s[3]), lap);
+            lap = fma2(splat(c.c2), fma2(splat(-6.0f), uc, s[2]), lap);
+            lap = fma2(splat(c.c1), fma2(splat(-6.0f), uc, s[1]), lap);
             const float2 gd = mul2(pair(wk.gxy, p), splat(gzk));
             const float2 ngd = mul2(pair(wk.gxy, p), splat(-gzk));   // -gd, exactly
             const float2 t = fma2(pair(wc, p), lap, fma2(splat(2.0f), uc, mul2(ngd, pair(upc, p))));
@@ -233,8 +325,8 @@ struct Kern {
         }
         float4 out = make_float4(o[0].x, o[0].y, o[1].x, o[1].y);
         if (wk.src_mask) {
-            for (int qs = 0; qs < a.src.n; ++qs) {
-                const SourceSample &ss = a.src.s[qs];
+            for (int qs = 0; qs < v.nsrc; ++qs) {
+                const SourceSample ss = v.src[qs];
                 if (((wk.src_mask >> qs) & 1u) && ss.k == k && ss.j == j) {
 #pragma unroll
                     for (int l = 0; l < 4; ++l)
@@ -249,16 +341,10 @@ struct Kern {
             if (wk.nvalid > 1) wk.out_k[1] = out.y;
             if (wk.nvalid > 2) wk.out_k[2] = out.z;
         }
-        wk.out_k += a.g.plane;
-        if (k == wk.rnext_k) {
-            while (wk.rcur < wk.rend && rec[wk.rcur].k == k) {
-                const RecEntry er = rec[wk.rcur];
-                if (er.owner == (int)threadIdx.x)
-                    a.traces[(long long)er.r * a.nt_max + a.trace_step] = comp(out, er.lane);
-                ++wk.rcur;
-            }
-            wk.rnext_k = wk.rcur < wk.rend ? rec[wk.rcur].k : INT_MAX;
-        }
+        wk.out_k += v.g.plane;
+        if (k == wk.rnext_k)
+            record_plane(out, 1.0f, k, &wk.rcur, wk.rend, &wk.rnext_k, v.rec, v.traces, v.nt_max,
+                         v.trace_step);
 #undef QI
 #undef BI
     }
@@ -274,10 +360,9 @@ struct Kern {
         }
     }
 
-    static __device__ void consumer(R &rg, const float *ringA, const float *ringB, float *up,
-                                    const StepArgs &a, int zb, int tiles_x, int ntiles,
-                                    int nitems, const int *rec_ptr, const RecEntry *rec) {
-        const Geom &g = a.g;
+    template <class S>
+    static __device__ void consumer(R &rg, const float *ringA, const float *ringB, const S &src,
+                                    const Coeffs &c, unsigned *status) {
         const int tid = threadIdx.x;
         const int tx = tid % (TX / 4);
         const int ty = tid / (TX / 4);
@@ -286,44 +371,46 @@ struct Kern {
         Walk wk;
         wk.gAw = wk.gAr = wk.gB = 0;
         wk.ok = true;
-        for (int item = blockIdx.x; item < nitems && wk.ok; item += gridDim.x) {
-            const Item it = item_of(item, tiles_x, ntiles, zb, g.nz, TX, TY);
+        for (int item = blockIdx.x; item < src.nitems() && wk.ok; item += gridDim.x) {
+            View v;
+            const Item it = src.view(item, &v);
+            const Geom &g = v.g;
             const int i = it.i0 + 4 * tx;
             const int j = it.j0 + ty;
             const bool col_ok = (j < g.ny) && (i < g.nx);
             wk.nvalid = col_ok ? min(4, g.nx - i) : 0;
             wk.gxy = make_float4(0.f, 0.f, 0.f, 0.f);
             if (col_ok) {
-                const float gyj = a.gy[j];
-                wk.gxy.x = a.gx[i] * gyj;
-                if (wk.nvalid > 1) wk.gxy.y = a.gx[i + 1] * gyj;
-                if (wk.nvalid > 2) wk.gxy.z = a.gx[i + 2] * gyj;
-                if (wk.nvalid > 3) wk.gxy.w = a.gx[i + 3] * gyj;
+                const float gyj = v.gy[j];
+                wk.gxy.x = v.gx[i] * gyj;
+                if (wk.nvalid > 1) wk.gxy.y = v.gx[i + 1] * gyj;
+                if (wk.nvalid > 2) wk.gxy.z = v.gx[i + 2] * gyj;
+                if (wk.nvalid > 3) wk.gxy.w = v.gx[i + 3] * gyj;
             }
             wk.src_mask = 0u;
-            for (int qs = 0; qs < a.src.n; ++qs) {
-                const SourceSample &ss = a.src.s[qs];
+            for (int qs = 0; qs < v.nsrc; ++qs) {
+                const SourceSample ss = v.src[qs];
                 if (ss.i >= it.i0 && ss.i < it.i0 + TX && ss.j >= it.j0 && ss.j < it.j0 + TY &&
                     ss.k >= it.z0 && ss.k < it.z1)
                     wk.src_mask |= 1u << qs;
             }
             wk.rcur = wk.rend = 0;
-            if (rec_ptr != nullptr) {
-                wk.rcur = rec_ptr[it.tile];
-                wk.rend = rec_ptr[it.tile + 1];
-                while (wk.rcur < wk.rend && rec[wk.rcur].k < it.z0) ++wk.rcur;
+            if (v.rec_ptr != nullptr) {
+                const int r = it.tile * (Cfg::kConsumers / 32) + (tid >> 5);
+                wk.rend = v.rec_ptr[r + 1];
+                wk.rcur = first_entry(v.rec, v.rec_ptr[r], wk.rend, it.z0);
             }
-            wk.rnext_k = wk.rcur < wk.rend ? rec[wk.rcur].k : INT_MAX;
-            wk.out_k = up + pidx(g, col_ok ? i : 0, col_ok ? j : 0, it.z0);
+            wk.rnext_k = wk.rcur < wk.rend ? v.rec[wk.rcur].k : INT_MAX;
+            wk.out_k = v.out + pidx(g, col_ok ? i : 0, col_ok ? j : 0, it.z0);
 #pragma unroll
             for (int d = 0; d < 2; ++d)
-                wk.gzb[d] = (it.z0 + d < it.z1) ? __ldg(a.gz + it.z0 + d) : 1.0f;
+                wk.gzb[d] = (it.z0 + d < it.z1) ? __ldg(v.gz + it.z0 + d) : 1.0f;
 
             // queue prologue: planes z0-4 .. z0+3; the first four are only
             // needed here and are released at once
 #pragma unroll
             for (int m = 0; m < 2 * kHalo; ++m) {
-                const float *sa = wait_a(wk, rg, ringA, wk.gAw, a.status);
+                const float *sa = wait_a(wk, rg, ringA, wk.gAw, status);
                 wk.q[m] = lds4(sa + offA);
                 ++wk.gAw;
             }
@@ -332,13 +419,13 @@ struct Kern {
                 warp_arrive(&rg.emptyA[wk.gAr & (NA - 1)]);
                 ++wk.gAr;
             }
-            if (!wk.ok) break;
+            if (!warp_all_ok(wk)) break;
 
             for (int kb = it.z0; kb < it.z1; kb += kUnroll) {
 #define WS_PLANE(RQ)                                                                         \
     if (kb + (RQ) >= it.z1) break;                                                           \
-    plane_step<RQ>(wk, rg, ringA, ringB, a, it, kb + (RQ), i, j, offA, offB, rec);          \
-    if (!wk.ok) break;
+    plane_step<RQ>(wk, rg, ringA, ringB, v, c, status, it, kb + (RQ), i, j, offA, offB);    \
+    if (!warp_all_ok(wk)) break;
                 WS_PLANE(0)
                 WS_PLANE(1)
                 WS_PLANE(2)
@@ -363,12 +450,9 @@ struct Kern {
     }
 };
 
-template <int TX, int TY, int NA, int NB, int MINB>
-__global__ void __launch_bounds__(StreamCfg<TX, TY, NA, NB>::kThreads, MINB)
-    step_stream_kernel(const __grid_constant__ StreamMaps maps, float *__restrict__ up,
-                       const __grid_constant__ StepArgs a, const int zb, const int tiles_x,
-                       const int ntiles, const int nitems, const int *__restrict__ rec_ptr,
-                       const RecEntry *__restrict__ rec) {
+// The body of a launch: ring set-up, the warp roles, and the drain.
+template <int TX, int TY, int NA, int NB, class S>
+__device__ __forceinline__ void stream_body(const S &src, const Coeffs &c, unsigned *status) {
     using K = Kern<TX, TY, NA, NB>;
     using Cfg = typename K::Cfg;
     extern __shared__ __align__(128) float smem[];
@@ -393,10 +477,9 @@ __global__ void __launch_bounds__(StreamCfg<TX, TY, NA, NB>::kThreads, MINB)
     __syncthreads();
 
     if (threadIdx.x >= Cfg::kConsumers) {
-        if (threadIdx.x == Cfg::kConsumers)
-            K::producer(rg, ringA, ringB, maps, a, zb, tiles_x, ntiles, nitems);
+        if (threadIdx.x == Cfg::kConsumers) K::producer(rg, ringA, ringB, src, status);
     } else {
-        K::consumer(rg, ringA, ringB, up, a, zb, tiles_x, ntiles, nitems, rec_ptr, rec);
+        K::consumer(rg, ringA, ringB, src, c, status);
     }
 
     // After an abort, wait (bounded) for the last copy issued into each slot
@@ -404,14 +487,49 @@ __global__ void __launch_bounds__(StreamCfg<TX, TY, NA, NB>::kThreads, MINB)
     __syncthreads();
     if (rg.abort && threadIdx.x == 0) {
         for (int s = 0; s < NA + NB; ++s) {
-            const int c = s < NA ? rg.issuedA[s] : rg.issuedB[s - NA];
+            const int cnt = s < NA ? rg.issuedA[s] : rg.issuedB[s - NA];
             uint64_t *bar = s < NA ? &rg.fullA[s] : &rg.fullB[s - NA];
-            if (c == 0) continue;
+            if (cnt == 0) continue;
             const unsigned long long t0 = global_ns();
-            while (!mbar_try_wait(bar, (unsigned)(c - 1) & 1u) && global_ns() - t0 < kWaitLimitNs) {
+            while (!mbar_try_wait(bar, (unsigned)(cnt - 1) & 1u) && global_ns() - t0 < kWaitLimitNs) {
             }
         }
     }
+}
+
+template <int TX, int TY, int NA, int NB, int MINB>
+__global__ void __launch_bounds__(StreamCfg<TX, TY, NA, NB>::kThreads, MINB)
+    step_stream_kernel(const __grid_constant__ StreamMaps maps, float *__restrict__ up,
+                       const __grid_constant__ StepArgs a, const int zb, const int tiles_x,
+                       const int ntiles, const int nitems, const int *__restrict__ rec_ptr,
+                       const RecEntry *__restrict__ rec) {
+    const OneGrid<TX, TY> src{maps, a, up, zb, tiles_x, ntiles, nitems, rec_ptr, rec};
+    stream_body<TX, TY, NA, NB>(src, a.c, a.status);
+}
+
+template <int TX, int TY, int NA, int NB, int MINB>
+__global__ void __launch_bounds__(StreamCfg<TX, TY, NA, NB>::kThreads, MINB)
+    step_batch_kernel(const BatchShot *__restrict__ shots, const int2 *__restrict__ items,
+                      const int nitems, const int t, const Coeffs c, unsigned *status) {
+    const ShotBatch<TX, TY> src{shots, items, nitems, t};
+    stream_body<TX, TY, NA, NB>(src, c, status);
+}
+
+// Resident CTAs per SM and SM count of a kernel (queried once per kernel).
+template <class KernFn>
+cudaError_t occupancy(KernFn kern, int threads, size_t smem, int *ctas_per_sm, int *sms) {
+    if (*ctas_per_sm != 0) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, n = 0, c = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, kern, threads, smem);
+    if (e != cudaSuccess) return e;
+    if (c < 1) return cudaErrorInvalidConfiguration;
+    *sms = n;
+    *ctas_per_sm = c;
+    return cudaSuccess;
 }
 
 template <int TX, int TY, int NA, int NB, int MINB>
@@ -420,25 +538,39 @@ cudaError_t launch_tile(const StreamMaps &maps, float *up, const StepArgs &a, in
     using Cfg = StreamCfg<TX, TY, NA, NB>;
     auto kern = step_stream_kernel<TX, TY, NA, NB, MINB>;
     static int ctas_per_sm = 0, sms = 0;
-    if (ctas_per_sm == 0) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)Cfg::kSmem);
-        if (e != cudaSuccess) return e;
-        int dev = 0;
-        e = cudaGetDevice(&dev);
-        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas_per_sm, kern, Cfg::kThreads,
-                                                              Cfg::kSmem);
-        if (e != cudaSuccess) return e;
-        if (ctas_per_sm < 1) return cudaErrorInvalidConfiguration;
-    }
+    cudaError_t e = occupancy(kern, Cfg::kThreads, Cfg::kSmem, &ctas_per_sm, &sms);
+    if (e != cudaSuccess) return e;
     const int tiles_x = (a.g.nx + TX - 1) / TX;
     const int ntiles = tiles_x * ((a.g.ny + TY - 1) / TY);
     const int nitems = ntiles * ((a.g.nz + zb - 1) / zb);
     const int grid = min(nitems, sms * ctas_per_sm);
     kern<<<grid, Cfg::kThreads, Cfg::kSmem, s>>>(maps, up, a, zb, tiles_x, ntiles, nitems, rec_ptr,
                                                  rec);
+    return cudaGetLastError();
+}
+
+template <int TX, int TY, int NA, int NB, int MINB>
+cudaError_t slots_of(bool batch, int *slots) {
+    using Cfg = StreamCfg<TX, TY, NA, NB>;
+    static int c1 = 0, n1 = 0, c2 = 0, n2 = 0;
+    cudaError_t e = batch ? occupancy(step_batch_kernel<TX, TY, NA, NB, MINB>, Cfg::kThreads,
+                                      Cfg::kSmem, &c2, &n2)
+                          : occupancy(step_stream_kernel<TX, TY, NA, NB, MINB>, Cfg::kThreads,
+                                      Cfg::kSmem, &c1, &n1);
+    if (e == cudaSuccess) *slots = batch ? c2 * n2 : c1 * n1;
+    return e;
+}
+
+template <int TX, int TY, int NA, int NB, int MINB>
+cudaError_t launch_batch_tile(const BatchShot *shots, const int2 *items, int nitems, int t,
+                              const Coeffs &c, unsigned *status, cudaStream_t s) {
+    using Cfg = StreamCfg<TX, TY, NA, NB>;
+    auto kern = step_batch_kernel<TX, TY, NA, NB, MINB>;
+    static int ctas_per_sm = 0, sms = 0;
+    cudaError_t e = occupancy(kern, Cfg::kThreads, Cfg::kSmem, &ctas_per_sm, &sms);
+    if (e != cudaSuccess) return e;
+    const int grid = min(nitems, sms * ctas_per_sm);
+    kern<<<grid, Cfg::kThreads, Cfg::kSmem, s>>>(shots, items, nitems, t, c, status);
     return cudaGetLastError();
 }
 
@@ -463,6 +595,31 @@ cudaError_t launch_step_stream(const CUtensorMap *tmap_u, const CUtensorMap *tma
     if (t.tx == 32 && t.ty == 16)
         return launch_tile<32, 16, WS_RING_A, 4, 3>(maps, up, a, t.zb, rec_ptr, rec, s);
     if (t.tx == 32 && t.ty == 8) return launch_tile<32, 8, 8, 4, 4>(maps, up, a, t.zb, rec_ptr, rec, s);
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace ws
+
+namespace ws {
+
+cudaError_t stream_slots(int tx, int ty, bool batch, int *slots) {
+    if (tx == 64 && ty == 32) return slots_of<64, 32, 8, 4, 1>(batch, slots);
+    if (tx == 64 && ty == 16) return slots_of<64, 16, 8, 4, 2>(batch, slots);
+    if (tx == 64 && ty == 8) return slots_of<64, 8, 8, 4, 3>(batch, slots);
+    if (tx == 32 && ty == 16) return slots_of<32, 16, WS_RING_A, 4, 3>(batch, slots);
+    if (tx == 32 && ty == 8) return slots_of<32, 8, 8, 4, 4>(batch, slots);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_step_batch(const BatchShot *shots, const int2 *items, int nitems, int t,
+                              const Coeffs &c, unsigned *status, int tx, int ty, cudaStream_t s) {
+    if (nitems <= 0) return cudaSuccess;
+    if (tx == 64 && ty == 32) return launch_batch_tile<64, 32, 8, 4, 1>(shots, items, nitems, t, c, status, s);
+    if (tx == 64 && ty == 16) return launch_batch_tile<64, 16, 8, 4, 2>(shots, items, nitems, t, c, status, s);
+    if (tx == 64 && ty == 8) return launch_batch_tile<64, 8, 8, 4, 3>(shots, items, nitems, t, c, status, s);
+    if (tx == 32 && ty == 16)
+        return launch_batch_tile<32, 16, WS_RING_A, 4, 3>(shots, items, nitems, t, c, status, s);
+    if (tx == 32 && ty == 8) return launch_batch_tile<32, 8, 8, 4, 4>(shots, items, nitems, t, c, status, s);
     return cudaErrorInvalidValue;
 }
 

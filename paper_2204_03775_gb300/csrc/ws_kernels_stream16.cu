@@ -285,16 +285,9 @@ struct Kern16 {
             }
         }
         wk.out_k += a.g.plane;
-        if (k == wk.rnext_k) {
-            while (wk.rcur < wk.rend && rec[wk.rcur].k == k) {
-                const RecEntry er = rec[wk.rcur];
-                if (er.owner == (int)threadIdx.x)
-                    a.traces[(long long)er.r * a.nt_max + a.trace_step] =
-                        comp(out, er.lane) * fc.out2true;
-                ++wk.rcur;
-            }
-            wk.rnext_k = wk.rcur < wk.rend ? rec[wk.rcur].k : INT_MAX;
-        }
+        if (k == wk.rnext_k)
+            record_plane(out, fc.out2true, k, &wk.rcur, wk.rend, &wk.rnext_k, rec, a.traces,
+                         a.nt_max, a.trace_step);
 #undef QI
 #undef BI
     }
@@ -344,9 +337,9 @@ struct Kern16 {
             }
             wk.rcur = wk.rend = 0;
             if (rec_ptr != nullptr) {
-                wk.rcur = rec_ptr[it.tile];
-                wk.rend = rec_ptr[it.tile + 1];
-                while (wk.rcur < wk.rend && rec[wk.rcur].k < it.z0) ++wk.rcur;
+                const int r = it.tile * (Cfg::kConsumers / 32) + (tid >> 5);
+                wk.rend = rec_ptr[r + 1];
+                wk.rcur = first_entry(rec, rec_ptr[r], wk.rend, it.z0);
             }
             wk.rnext_k = wk.rcur < wk.rend ? rec[wk.rcur].k : INT_MAX;
             wk.out_k = up + pidx(g, col_ok ? i : 0, col_ok ? j : 0, it.z0);
@@ -366,13 +359,13 @@ struct Kern16 {
                 warp_arrive(&rg.emptyA[wk.gAr & (NA - 1)]);
                 ++wk.gAr;
             }
-            if (!wk.ok) break;
+            if (!warp_all_ok(wk)) break;
 
             for (int kb = it.z0; kb < it.z1; kb += kUnroll16) {
 #define WS_PLANE(RQ)                                                                           \
     if (kb + (RQ) >= it.z1) break;                                                             \
     plane_step<RQ>(wk, rg, ringA, ringB, a, fc, it, kb + (RQ), i, j, offA, offB, rec);         \
-    if (!wk.ok) break;
+    if (!warp_all_ok(wk)) break;
                 WS_PLANE(0)
                 WS_PLANE(1)
                 WS_PLANE(2)

@@ -2,6 +2,8 @@
 // TMA tensor copies, whole 128/64-bit shared loads, packed FP32x2 arithmetic.
 #pragma once
 
+#include <climits>
+
 #include "ws_internal.h"
 
 namespace ws {
@@ -136,6 +138,60 @@ static __device__ __forceinline__ Item item_of(int item, int tiles_x, int ntiles
     it.z0 = blk * zb;
     it.z1 = min(it.z0 + zb, nz);
     return it;
+}
+
+// Receivers: each warp of a streaming CTA owns a range of the receiver
+// table sorted by plane k (the receivers whose cell one of its threads
+// computes). first_entry skips to the first entry at or below plane z0 by
+// binary search; record_plane stores the values of plane k: lane q takes
+// entry cur + q, fetches the owning thread's cell by shuffle, and stores it.
+// Every lane of the warp calls both with the same range.
+static __device__ __forceinline__ int first_entry(const RecEntry *rec, int lo, int hi, int z0) {
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (rec[mid].k < z0)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+static __device__ __forceinline__ void record_plane(const float4 &out, float scale, int k,
+                                                    int *rcur, int rend, int *rnext_k,
+                                                    const RecEntry *rec, float *traces, int nt_max,
+                                                    long long trace_step) {
+    const int lane = threadIdx.x & 31;
+    int cur = *rcur;
+    for (;;) {
+        const int idx = cur + lane;
+        RecEntry e{INT_MAX, 0, 0, 0};
+        if (idx < rend) e = rec[idx];
+        const bool take = e.k == k;
+        const int src = e.owner & 31;
+        const float v0 = __shfl_sync(0xffffffffu, out.x, src);
+        const float v1 = __shfl_sync(0xffffffffu, out.y, src);
+        const float v2 = __shfl_sync(0xffffffffu, out.z, src);
+        const float v3 = __shfl_sync(0xffffffffu, out.w, src);
+        if (take) {
+            const float v = e.lane == 0 ? v0 : e.lane == 1 ? v1 : e.lane == 2 ? v2 : v3;
+            traces[(long long)e.r * nt_max + trace_step] = v * scale;
+        }
+        const int n = __popc(__ballot_sync(0xffffffffu, take));
+        cur += n;
+        if (n < 32) break;
+    }
+    *rcur = cur;
+    *rnext_k = cur < rend ? rec[cur].k : INT_MAX;
+}
+
+// A consumer leaves its loops only together with its whole warp (the
+// receiver shuffles and the warp-wide arrives need every lane): after a
+// failed wait in any lane, every lane's walk stops.
+template <class W>
+static __device__ __forceinline__ bool warp_all_ok(W &wk) {
+    wk.ok = __all_sync(0xffffffffu, wk.ok);
+    return wk.ok;
 }
 
 // Shared-memory state of one CTA.

@@ -20,6 +20,19 @@ hundreds to a thousand cells per axis, 1000 steps, Section IV):
   every face, dt at CFL 0.4, one 10 Hz Ricker at (nx/2, ny/2, 20) and a
   32 x 32 receiver grid on the plane k = 20; 1024^3 and 1000 steps is the
   benchmark's workload, smaller sizes are parity cases.
+* ``adjoint_survey`` -- gradient workload: the layered model as the start
+  (background) model, the true model the background times
+  1 + 0.1 exp(-|x - c|^2 / (2 s^2)) (a +10% Gaussian blob, s = n/12, centre c
+  drawn from the seed inside the middle half of the grid), a 4 x 4 grid of
+  10 Hz Ricker shots and a 128 x 128 receiver grid on the plane k = 20,
+  a 20-cell absorbing layer, dt at CFL 0.4 of the faster (true) model;
+  256^3 with 800 steps is the full size.
+* ``batched_shots`` -- 64 independent shots on grids whose sizes are drawn
+  from the seed (nx, ny uniform in [96, 320], nz in [96, 256]), each with
+  its own smooth random model in [1500, 4500] m/s (``smooth_random_velocity``,
+  seeded per shot), a 16-cell absorbing layer, dt at CFL 0.4 of 4500 m/s, one
+  Ricker source (f0 uniform in [8, 20] Hz) at a random cell of the upper
+  quarter and an 8 x 8 receiver grid on the plane k = 16; 500 steps each.
 """
 
 from __future__ import annotations
@@ -120,3 +133,59 @@ def smooth_random_velocity(shape, seed: int, vmin: float = 1500.0, vmax: float =
     n = smooth_noise(shape, seed, spacing=spacing)
     v = 0.5 * (vmin + vmax) + 0.5 * (vmax - vmin) * n
     return np.clip(v, vmin, vmax).astype(np.float32)
+
+
+@dataclass
+class AdjointSurvey:
+    name: str
+    nx: int
+    ny: int
+    nz: int
+    h: float
+    dt: float
+    nt: int
+    vel_true: np.ndarray                 # [nz][ny][nx] float32, m/s
+    vel_start: np.ndarray                # the background model
+    shots: list                          # per shot: a list of (i, j, k, f0, t0, amp)
+    receivers: np.ndarray                # [nrec][3] int32, shared by every shot
+    sponge: tuple = (20, 0.015)
+
+
+def adjoint_survey(n: int = 256, nt: int = 800, shots_side: int = 4, rec_side: int = 128,
+                   h: float = 10.0, nb: int = 20, a: float = 0.015, f0: float = 10.0,
+                   seed: int = 2204) -> AdjointSurvey:
+    bg = layered_model(n, n, n, seed=seed)
+    rng = np.random.Generator(np.random.PCG64(seed + 1))
+    c = rng.uniform(n / 4, 3 * n / 4, 3)              # blob centre (k, j, i)
+    s = n / 12.0
+    k, j, i = np.ogrid[:n, :n, :n]
+    r2 = (k - c[0]) ** 2 + (j - c[1]) ** 2 + (i - c[2]) ** 2
+    true = (bg * (1.0 + 0.1 * np.exp(-r2 / (2.0 * s * s)))).astype(np.float32)
+    dt = cfl_dt(float(true.max()), h)
+    plane = min(nb, n - 1)
+    margin = min(nb, n // 4)
+    side = min(rec_side, n - 2 * margin)
+    rec = surface_receivers(n, n, plane, side, margin)
+    pos = surface_receivers(n, n, plane, shots_side, margin)
+    shots = [[(int(p[0]), int(p[1]), int(p[2]), f0, 1.0 / f0, 1.0)] for p in pos]
+    return AdjointSurvey(f"adjoint_survey_{n}^3", n, n, n, h, dt, nt, true, bg, shots, rec,
+                         sponge=(nb, a))
+
+
+def batched_shots(nshots: int = 64, nt: int = 500, lo=(96, 96, 96), hi=(320, 320, 256),
+                  h: float = 10.0, nb: int = 16, a: float = 0.02, seed: int = 2204) -> list:
+    """Workloads of independent shots on uneven grids (sizes (nx, ny, nz) in [lo, hi])."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    dt = cfl_dt(4500.0, h)
+    out = []
+    for q in range(nshots):
+        nx, ny, nz = (int(rng.integers(lo[d], hi[d] + 1)) for d in range(3))
+        vel = smooth_random_velocity((nz, ny, nx), seed + 1000 + q, spacing=8)
+        plane = min(nb, nz - 1)
+        src = [(int(rng.integers(nb, nx - nb)), int(rng.integers(nb, ny - nb)),
+                int(rng.integers(plane, max(plane + 1, nz // 4))), float(rng.uniform(8.0, 20.0)),
+                0.1, 1.0)]
+        rec = surface_receivers(nx, ny, plane, 8, nb)
+        out.append(Workload(f"shot{q}_{nx}x{ny}x{nz}", nx, ny, nz, h, dt, nt, vel, sources=src,
+                            receivers=rec, sponge=(nb, a)))
+    return out
