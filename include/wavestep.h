@@ -207,12 +207,16 @@ int ws_energy_noalloc(const float *u, const float *u_prev, const float *v, int n
  * W G r^k (Lap' = h^2 Lap, r^k injected at the receivers), so the step
  * kernels advance rho; dJ/dm = -V^2 sum_n rho^{n+1} (Lap' u^n), plus
  * -V^2 sum_n rho^{n+1} h^2 s_n / G at each source cell. The states u^n are
- * recomputed from ceil(N / C) - 1 checkpoint pairs, C = ceil(sqrt(N)),
- * N = nt_max: two forward passes and one backward pass in all.
+ * recomputed, segment by segment, from ceil(N / C) - 1 checkpoint pairs,
+ * C = ceil(sqrt(N)), N = nt_max; the recomputing steps store the stencil
+ * sums Lap' u^n of their segment (the float values the step used) for the
+ * imaging: two forward passes and one backward pass in all.
  *
  * Needs a velocity model, receivers and FP32 storage, else STATE. Device
- * scratch, allocated for the call and freed before it returns: about
- * 3 sqrt(N) + 3 padded fields, 8 bytes per cell, and two trace arrays.
+ * scratch: about 3 sqrt(N) + 4 padded fields, 12 bytes per cell and two
+ * trace arrays, allocated by the first call and kept by the handle for the
+ * next ones while N, the receiver count and the tiling stay the same (freed
+ * by ws_destroy).
  * Afterwards the handle holds the forward run's final state (step N) and
  * its traces. Synchronizes the stream. Errors: BADARG, STATE, OOM, CUDA,
  * TIMEOUT. */

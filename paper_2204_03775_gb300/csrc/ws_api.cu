@@ -10,6 +10,7 @@
 #include <mutex>
 #include <new>
 #include <tuple>
+#include <type_traits>
 #include <vector>
 
 #include "ws_internal.h"
@@ -126,6 +127,9 @@ struct ws_handle {
     ws::Scale16 *scale = nullptr;
     CUtensorMap t16_halo[2], t16_tile[2], t16_w;  // t16_w: FP32 model, 16-bit tile box
     double wmax = 0.0;         // max (V dt / h)^2 of the model
+
+    // device scratch of ws_adjoint_gradient, kept for the next call
+    struct AdjointCache *adj = nullptr;
 };
 
 // A group of handles advanced together: one persistent launch per step
@@ -154,6 +158,29 @@ struct ws_batch {
     Cand cfg{0, 0, -1};                // what the item table was built for
     float best_ms = 1e30f;
     long long launches = 0;
+};
+
+// A padded FP32 field with the streaming kernel's two boxes on it.
+struct MappedField {
+    float *p = nullptr;
+    CUtensorMap halo, tile;
+};
+
+// Scratch of ws_adjoint_gradient: checkpoint pairs, the states of one
+// segment, the two adjoint levels, the gradient accumulator and the trace
+// arrays. Reused while the step count, receivers and tiling stay the same.
+struct AdjointCache {
+    int N = -1, nrec = -1, kern = -1, tx = 0, ty = 0;
+    std::vector<void *> mem;        // everything below, for cudaFree
+    std::vector<float *> ck;
+    std::vector<float *> lap;       // L u^n of the segment's steps
+    MappedField ring[2], rho[2];    // recomputed u^n / u^{n-1}; rho^{k+1} / rho^{k+2}
+    double *acc = nullptr, *partials = nullptr;
+    float *r = nullptr, *dd = nullptr, *grad = nullptr;
+    int *rec = nullptr;
+    ~AdjointCache() {
+        for (void *p : mem) cudaFree(p);
+    }
 };
 
 namespace {
@@ -469,6 +496,7 @@ void destroy(ws_t ws) {
     cudaFree(ws->buf16[1]);
     cudaFree(ws->scale);
     free_receivers(ws);
+    delete ws->adj;
     delete ws;
 }
 
@@ -496,11 +524,6 @@ std::mutex g_tune_mutex;
 std::map<std::tuple<int, int, int>, ws::StreamTiling> g_tune_cache;
 
 
-// A padded FP32 field with the streaming kernel's two boxes on it.
-struct MappedField {
-    float *p = nullptr;
-    CUtensorMap halo, tile;
-};
 
 // Device scratch of one call: freed, after the stream drains, on every return.
 struct Scratch {
@@ -522,16 +545,6 @@ struct Scratch {
     }
 };
 
-int alloc_field(ws_t ws, Scratch &sc, MappedField *f, bool maps, bool zero) {
-    const size_t fb = field_bytes(ws->g);
-    WS_CUDA(sc.alloc(&f->p, fb), "cudaMalloc adjoint field");
-    if (zero) WS_CUDA(cudaMemsetAsync(f->p, 0, fb, ws->stream), "zero adjoint field");
-    if (!maps) return WS_OK;
-    const int tx = ws->tiling.tx, ty = ws->tiling.ty;
-    int rc = encode_map(&f->halo, f->p, ws->g, tx + 2 * ws::kHalo, ty + 2 * ws::kHalo);
-    if (rc == WS_OK) rc = encode_map(&f->tile, f->p, ws->g, tx, ty);
-    return rc;
-}
 
 }  // namespace
 
@@ -957,38 +970,90 @@ int ws_adjoint_gradient(ws_t ws, const float *data, int mode, float *grad_m, dou
     const size_t ncell = size_t(g.nx) * g.ny * g.nz;
     const size_t ntr = size_t(ws->nrec) * N;
     const cudaStream_t st = ws->stream;
-    Scratch sc(st);
-
-    // checkpoints (u^{jC}, u^{jC-1}), j = 1 .. nck-1; segment states; rho
-    std::vector<float *> ck(2 * size_t(nck - 1), nullptr);
-    for (auto &c : ck) WS_CUDA(sc.alloc(&c, fb), "cudaMalloc checkpoint");
-    std::vector<MappedField> seg(C);
-    MappedField segprev, rho[2];
-    for (auto &f : seg)
-        if ((rc = alloc_field(ws, sc, &f, maps, true)) != WS_OK) return rc;
-    if ((rc = alloc_field(ws, sc, &segprev, maps, true)) != WS_OK) return rc;
-    for (auto &f : rho)
-        if ((rc = alloc_field(ws, sc, &f, maps, true)) != WS_OK) return rc;
-    double *acc = nullptr, *partials = nullptr;
-    float *r = nullptr, *grad = grad_m;
+    AdjointCache *ac = ws->adj;
+    if (!ac || ac->N != N || ac->nrec != ws->nrec || ac->kern != kern ||
+        (maps && (ac->tx != ws->tiling.tx || ac->ty != ws->tiling.ty))) {
+        WS_CUDA(cudaStreamSynchronize(st), "ws_adjoint_gradient");
+        delete ws->adj;
+        ws->adj = nullptr;
+        ac = new (std::nothrow) AdjointCache();
+        if (!ac) return fail(WS_ERR_OOM, "ws_adjoint_gradient: host allocation failed");
+        ws->adj = ac;
+        auto grab = [&](auto **p, size_t bytes) -> cudaError_t {
+            void *q = nullptr;
+            cudaError_t e = cudaMalloc(&q, bytes);
+            if (e == cudaSuccess) {
+                ac->mem.push_back(q);
+                *p = static_cast<std::remove_reference_t<decltype(**p)> *>(q);
+            }
+            return e;
+        };
+        auto field = [&](MappedField *f) -> int {
+            WS_CUDA(grab(&f->p, fb), "cudaMalloc adjoint field");
+            WS_CUDA(cudaMemsetAsync(f->p, 0, fb, st), "zero adjoint field");
+            if (!maps) return WS_OK;
+            const int tx = ws->tiling.tx, ty = ws->tiling.ty;
+            int r2 = encode_map(&f->halo, f->p, g, tx + 2 * ws::kHalo, ty + 2 * ws::kHalo);
+            if (r2 == WS_OK) r2 = encode_map(&f->tile, f->p, g, tx, ty);
+            return r2;
+        };
+        // checkpoints (u^{jC}, u^{jC-1}), j = 1 .. nck-1; segment states; rho
+        ac->ck.assign(2 * size_t(nck - 1), nullptr);
+        for (auto &c : ac->ck) {
+            cudaError_t e = grab(&c, fb);
+            if (e != cudaSuccess) {
+                delete ws->adj;
+                ws->adj = nullptr;
+                return cuda_fail(e, "cudaMalloc checkpoint");
+            }
+        }
+        ac->lap.assign(C, nullptr);
+        cudaError_t e = cudaSuccess;
+        for (auto &f : ac->lap) {   // zeroed: the steps write the interior only
+            if (e == cudaSuccess) e = grab(&f, fb);
+            if (e == cudaSuccess) e = cudaMemsetAsync(f, 0, fb, st);
+        }
+        int r3 = e == cudaSuccess ? WS_OK : cuda_fail(e, "cudaMalloc adjoint field");
+        for (auto &f : ac->ring)
+            if (r3 == WS_OK) r3 = field(&f);
+        for (auto &f : ac->rho)
+            if (r3 == WS_OK) r3 = field(&f);
+        if (r3 == WS_OK) e = grab(&ac->acc, 2 * fb);   // FP64, padded layout
+        if (r3 == WS_OK && e == cudaSuccess) e = grab(&ac->partials, sizeof(double) * (ws::residual_partial_count() + 1));
+        if (r3 == WS_OK && e == cudaSuccess) e = grab(&ac->r, sizeof(float) * ntr);
+        if (r3 == WS_OK && e == cudaSuccess) e = grab(&ac->dd, sizeof(float) * ntr);
+        if (r3 == WS_OK && e == cudaSuccess) e = grab(&ac->grad, sizeof(float) * ncell);
+        if (r3 == WS_OK && e == cudaSuccess) e = grab(&ac->rec, sizeof(int) * 3 * ws->nrec);
+        if (r3 != WS_OK || e != cudaSuccess) {
+            delete ws->adj;
+            ws->adj = nullptr;
+            return r3 != WS_OK ? r3 : cuda_fail(e, "cudaMalloc adjoint scratch");
+        }
+        ac->N = N;
+        ac->nrec = ws->nrec;
+        ac->kern = kern;
+        ac->tx = ws->tiling.tx;
+        ac->ty = ws->tiling.ty;
+    } else {
+        for (auto &f : ac->rho) WS_CUDA(cudaMemsetAsync(f.p, 0, fb, st), "zero adjoint field");
+    }
+    std::vector<float *> &ck = ac->ck;
+    std::vector<float *> &lap = ac->lap;
+    MappedField *ring = ac->ring;
+    MappedField *rho = ac->rho;
+    double *acc = ac->acc, *partials = ac->partials;
+    float *r = ac->r, *grad = on_device ? grad_m : ac->grad;
     const float *d = data;
-    int *rec = nullptr;
+    int *rec = ac->rec;
     const int np = ws::residual_partial_count();
-    WS_CUDA(sc.alloc(&acc, sizeof(double) * ncell), "cudaMalloc gradient accumulator");
-    WS_CUDA(sc.alloc(&partials, sizeof(double) * (np + 1)), "cudaMalloc misfit partials");
-    WS_CUDA(sc.alloc(&r, sizeof(float) * ntr), "cudaMalloc residual");
-    WS_CUDA(sc.alloc(&rec, sizeof(int) * 3 * ws->nrec), "cudaMalloc receivers");
-    WS_CUDA(cudaMemsetAsync(acc, 0, sizeof(double) * ncell, st), "zero gradient accumulator");
+    WS_CUDA(cudaMemsetAsync(acc, 0, 2 * fb, st), "zero gradient accumulator");
     WS_CUDA(cudaMemcpyAsync(rec, ws->rec_ijk.data(), sizeof(int) * 3 * ws->nrec,
                             cudaMemcpyHostToDevice, st),
             "upload receivers");
     if (!on_device) {
-        float *dd = nullptr;
-        WS_CUDA(sc.alloc(&dd, sizeof(float) * ntr), "cudaMalloc observed data");
-        WS_CUDA(cudaMemcpyAsync(dd, data, sizeof(float) * ntr, cudaMemcpyHostToDevice, st),
+        WS_CUDA(cudaMemcpyAsync(ac->dd, data, sizeof(float) * ntr, cudaMemcpyHostToDevice, st),
                 "upload observed data");
-        d = dd;
-        WS_CUDA(sc.alloc(&grad, sizeof(float) * ncell), "cudaMalloc gradient");
+        d = ac->dd;
     }
 
     // 1. forward from rest, recording the traces and the checkpoints
@@ -1023,24 +1088,29 @@ int ws_adjoint_gradient(ws_t ws, const float *data, int mode, float *grad_m, dou
 
     // 3. backward: rho^k, k = N .. 1, segment by segment, the segment's
     // states recomputed from its checkpoint
-    const ws::Coeffs cf{(float)kW1, (float)kW2, (float)kW3, (float)kW4};
     int rc_cur = 0;   // rho[rc_cur] = rho^{k+1}, rho[1 - rc_cur] = rho^{k+2}
     for (int j = nck - 1; j >= 0; --j) {
         const int n0 = j * C, n1 = std::min(n0 + C, N);
+        // u^{n0}, u^{n0-1} into the ring, then steps n0 .. n1-1, each storing
+        // L u^n into lap[n - n0] (u^{n1} itself is not needed)
         if (j == 0) {
-            WS_CUDA(cudaMemsetAsync(seg[0].p, 0, fb, st), "zero initial state");
-            WS_CUDA(cudaMemsetAsync(segprev.p, 0, fb, st), "zero initial state");
+            WS_CUDA(cudaMemsetAsync(ring[0].p, 0, fb, st), "zero initial state");
+            WS_CUDA(cudaMemsetAsync(ring[1].p, 0, fb, st), "zero initial state");
         } else {
-            WS_CUDA(cudaMemcpyAsync(seg[0].p, ck[2 * (j - 1)], fb, cudaMemcpyDeviceToDevice, st),
+            WS_CUDA(cudaMemcpyAsync(ring[0].p, ck[2 * (j - 1)], fb, cudaMemcpyDeviceToDevice, st),
                     "restore checkpoint");
-            WS_CUDA(cudaMemcpyAsync(segprev.p, ck[2 * (j - 1) + 1], fb, cudaMemcpyDeviceToDevice, st),
+            WS_CUDA(cudaMemcpyAsync(ring[1].p, ck[2 * (j - 1) + 1], fb, cudaMemcpyDeviceToDevice, st),
                     "restore checkpoint");
         }
-        for (int t = 0; t + 1 < n1 - n0; ++t) {
-            const MappedField &um = t == 0 ? segprev : seg[t - 1];
-            rc = step_fp32(ws, a, kern, tiling, seg[t].p, &seg[t].halo, um.p, &um.tile,
-                           seg[t + 1].p, n0 + t, true, false);
+        int uc = 0;   // ring[uc] = u^n
+        for (int t = 0; t < n1 - n0; ++t) {
+            MappedField &un = ring[uc], &um = ring[1 - uc];
+            a.lap = lap[t];
+            rc = step_fp32(ws, a, kern, tiling, un.p, &un.halo, um.p, &um.tile, um.p, n0 + t, true,
+                           false);
+            a.lap = nullptr;
             if (rc != WS_OK) return rc;
+            uc = 1 - uc;
         }
         for (int k = n1; k > n0; --k) {
             MappedField &r1 = rho[rc_cur], &r2 = rho[1 - rc_cur];
@@ -1053,7 +1123,7 @@ int ws_adjoint_gradient(ws_t ws, const float *data, int mode, float *grad_m, dou
                     "adjoint injection kernel");
             ws::Sources src{};
             sources_of_step(ws, k - 1, &src);
-            WS_CUDA(ws::launch_imaging(rho[rc_cur].p, seg[k - 1 - n0].p, g, cf, src, ws->gx, ws->gy,
+            WS_CUDA(ws::launch_imaging(rho[rc_cur].p, lap[k - 1 - n0], g, src, ws->gx, ws->gy,
                                        ws->gz, acc, st),
                     "gradient imaging kernel");
             ws->launches += 2;

@@ -93,6 +93,7 @@ struct StepArgs {
     int nt_max;
     long long trace_step;        // column of this step in traces
     unsigned *status;            // device status word
+    float *lap;                  // if not null: receives the stencil sum L u^n (padded field)
 };
 
 // Launchers (stream-ordered, no synchronization).
@@ -183,11 +184,12 @@ cudaError_t launch_residual(const float *traces, const float *d_obs, long long n
 cudaError_t launch_inject(float *rho, const float *w, const float *gx, const float *gy,
                           const float *gz, const Geom &g, const int *rec_ijk, int nrec,
                           const float *r, int nt, int col, cudaStream_t s);
-// acc (unpadded FP64) += rho * L u, plus rho * amp / G at source cells.
-cudaError_t launch_imaging(const float *rho, const float *u, const Geom &g, const Coeffs &c,
-                           const Sources &src, const float *gx, const float *gy, const float *gz,
-                           double *acc, cudaStream_t s);
-// grad (unpadded float) = -V^2 acc, V^2 = W (h / dt)^2.
+// acc (FP64, padded layout) += rho * lapu (the stencil sum L u^n a step
+// stored), plus rho * amp / G at source cells.
+cudaError_t launch_imaging(const float *rho, const float *lapu, const Geom &g, const Sources &src,
+                           const float *gx, const float *gy, const float *gz, double *acc,
+                           cudaStream_t s);
+// grad (unpadded float) = -V^2 acc (padded), V^2 = W (h / dt)^2.
 cudaError_t launch_finalize_gradient(const double *acc, const float *w, const Geom &g,
                                      double h_over_dt2, float *grad, cudaStream_t s);
 

@@ -76,48 +76,67 @@ __global__ void inject_kernel(float *__restrict__ rho, const float *__restrict__
     atomicAdd(&rho[p], w[p] * gd * r[(long long)q * nt + col]);
 }
 
-// acc += rho * L u (the steppers' zero-sum float stencil), and at source
-// cells rho * (h^2 s_n) / G; acc unpadded FP64.
+// acc += rho * (L u) with L u the stencil sum the step kernel stored while
+// recomputing u^{n+1} (the same float value the step used), and at source
+// cells rho * (h^2 s_n) / G. acc is FP64 in the padded layout, so a
+// thread's 4 consecutive x cells are one float4 of rho and of L u and two
+// double2 of acc. A block covers 128 x 8 cells of one plane; one thread
+// finds the block's sources first.
 __global__ void __launch_bounds__(256) imaging_kernel(const float *__restrict__ rho,
-                                                      const float *__restrict__ u, Geom g,
-                                                      Coeffs c, Sources src,
-                                                      const float *__restrict__ gx,
+                                                      const float *__restrict__ lapu, Geom g,
+                                                      Sources src, const float *__restrict__ gx,
                                                       const float *__restrict__ gy,
                                                       const float *__restrict__ gz,
                                                       double *__restrict__ acc) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const int k = blockIdx.z;
-    if (i >= g.nx || j >= g.ny) return;
-    const long long p = pidx(g, i, j, k);
-    const long long sy = g.pnx, sz = g.plane;
-    const float uc = u[p];
-    float s[5];
-#pragma unroll
-    for (int m = 1; m <= 4; ++m)
-        s[m] = ((u[p + m] + u[p - m]) + (u[p + m * sy] + u[p - m * sy])) + (u[p + m * sz] + u[p - m * sz]);
-    float lap = c.c4 * fmaf(-6.0f, uc, s[4]);
-    lap = fmaf(c.c3, fmaf(-6.0f, uc, s[3]), lap);
-    lap = fmaf(c.c2, fmaf(-6.0f, uc, s[2]), lap);
-    lap = fmaf(c.c1, fmaf(-6.0f, uc, s[1]), lap);
-    const float rv = rho[p];
-    double term = (double)rv * (double)lap;
-    for (int q = 0; q < src.n; ++q) {
-        const SourceSample &ss = src.s[q];
-        if (ss.i == i && ss.j == j && ss.k == k)
-            term += (double)rv * (double)ss.amp / ((double)gx[i] * gy[j] * gz[k]);
+    __shared__ unsigned mask;
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        unsigned m = 0;
+        const int i0 = 4 * blockIdx.x * blockDim.x, j0 = blockIdx.y * blockDim.y;
+        for (int q = 0; q < src.n; ++q) {
+            const SourceSample &ss = src.s[q];
+            if (ss.k == k && ss.j >= j0 && ss.j < j0 + (int)blockDim.y && ss.i >= i0 &&
+                ss.i < i0 + 4 * (int)blockDim.x)
+                m |= 1u << q;
+        }
+        mask = m;
     }
-    acc[((long long)k * g.ny + j) * g.nx + i] += term;
+    __syncthreads();
+    if (i >= g.nx || j >= g.ny) return;
+    const long long p = pidx(g, i, j, k);   // a multiple of 4: rows start on 32-cell lines
+    const float4 r4 = *reinterpret_cast<const float4 *>(rho + p);
+    const float4 l4 = __ldcs(reinterpret_cast<const float4 *>(lapu + p));
+    double2 a01 = *reinterpret_cast<const double2 *>(acc + p);
+    double2 a23 = *reinterpret_cast<const double2 *>(acc + p + 2);
+    double t[4] = {(double)r4.x * (double)l4.x, (double)r4.y * (double)l4.y,
+                   (double)r4.z * (double)l4.z, (double)r4.w * (double)l4.w};
+    const float rv[4] = {r4.x, r4.y, r4.z, r4.w};
+    for (unsigned m = mask; m; m &= m - 1) {
+        const SourceSample &ss = src.s[__ffs(m) - 1];
+        const int l = ss.i - i;
+        if (ss.j == j && l >= 0 && l < 4)
+            t[l] += (double)rv[l] * (double)ss.amp / ((double)gx[ss.i] * gy[j] * gz[k]);
+    }
+    // cells past nx (x padding: zero in rho and in L u) accumulate zeros
+    a01.x += t[0];
+    a01.y += t[1];
+    a23.x += t[2];
+    a23.y += t[3];
+    *reinterpret_cast<double2 *>(acc + p) = a01;
+    *reinterpret_cast<double2 *>(acc + p + 2) = a23;
 }
 
-// grad_m = -V^2 acc, V^2 = W (h/dt)^2; unpadded float output.
+// grad_m = -V^2 acc, V^2 = W (h/dt)^2; acc padded, unpadded float output.
 __global__ void finalize_kernel(const double *__restrict__ acc, const float *__restrict__ w,
                                 Geom g, double h_over_dt2, float *__restrict__ grad) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y, k = blockIdx.z;
     if (i >= g.nx) return;
     const long long o = ((long long)k * g.ny + j) * g.nx + i;
-    grad[o] = (float)(-(double)w[pidx(g, i, j, k)] * h_over_dt2 * acc[o]);
+    const long long p = pidx(g, i, j, k);
+    grad[o] = (float)(-(double)w[p] * h_over_dt2 * acc[p]);
 }
 
 }  // namespace
@@ -142,12 +161,12 @@ cudaError_t launch_inject(float *rho, const float *w, const float *gx, const flo
     return cudaGetLastError();
 }
 
-cudaError_t launch_imaging(const float *rho, const float *u, const Geom &g, const Coeffs &c,
-                           const Sources &src, const float *gx, const float *gy, const float *gz,
-                           double *acc, cudaStream_t s) {
+cudaError_t launch_imaging(const float *rho, const float *lapu, const Geom &g, const Sources &src,
+                           const float *gx, const float *gy, const float *gz, double *acc,
+                           cudaStream_t s) {
     dim3 block(32, 8, 1);
-    dim3 grid((g.nx + 31) / 32, (g.ny + 7) / 8, g.nz);
-    imaging_kernel<<<grid, block, 0, s>>>(rho, u, g, c, src, gx, gy, gz, acc);
+    dim3 grid((g.nx + 127) / 128, (g.ny + 7) / 8, g.nz);
+    imaging_kernel<<<grid, block, 0, s>>>(rho, lapu, g, src, gx, gy, gz, acc);
     return cudaGetLastError();
 }
 

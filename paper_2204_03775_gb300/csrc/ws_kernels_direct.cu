@@ -40,6 +40,7 @@ __global__ void __launch_bounds__(256) step_direct_kernel(const float *__restric
     lap = fmaf(a.c.c2, d[2], lap);
     lap = fmaf(a.c.c1, d[1], lap);
 
+    if (a.lap) a.lap[p] = lap;
     const float wc = w[p];
     const float gd = a.gx[i] * a.gy[j] * a.gz[k];
     float un = gd * fmaf(wc, lap, fmaf(2.0f, uc, -gd * up[p]));

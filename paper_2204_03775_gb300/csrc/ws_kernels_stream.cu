@@ -93,13 +93,16 @@ struct View {
     int nt_max;
     long long trace_step;
     float *out;                // u^{n+1} field (padded)
+    long long lap_delta;       // L u^n goes to out + lap_delta (0: not stored)
     const int *rec_ptr;        // per-tile receiver ranges, or null
     const RecEntry *rec;
 };
 
-// Items of one grid; everything comes from kernel parameters.
-template <int TX, int TY>
+// Items of one grid; everything comes from kernel parameters. kLap: the
+// launch also stores the stencil sum L u^n (into a.lap).
+template <int TX, int TY, bool kLap>
 struct OneGrid {
+    static constexpr bool kStoreLap = kLap;
     const StreamMaps &mp;
     const StepArgs &a;
     float *up;
@@ -122,6 +125,7 @@ struct OneGrid {
         v->nt_max = a.nt_max;
         v->trace_step = a.trace_step;
         v->out = up;
+        v->lap_delta = kLap ? a.lap - up : 0;
         v->rec_ptr = rec_ptr;
         v->rec = rec;
         return item_of(item, tiles_x, ntiles, zb, a.g.nz, TX, TY);
@@ -132,6 +136,7 @@ struct OneGrid {
 // the run; shot s reads u^n from buf[cur0 ^ (t & 1)].
 template <int TX, int TY>
 struct ShotBatch {
+    static constexpr bool kStoreLap = false;
     const BatchShot *shots;
     const int2 *items;
     int n, t;
@@ -158,6 +163,7 @@ struct ShotBatch {
         v->nt_max = s.nt_max;
         v->trace_step = s.trace_col0 + t;
         v->out = s.buf[1 - p];
+        v->lap_delta = 0;
         v->rec_ptr = s.rec_ptr;
         v->rec = s.rec;
         return item_of(e.y, s.tiles_x, s.ntiles, s.zb, s.g.nz, TX, TY);
@@ -245,7 +251,7 @@ struct Kern {
 
     // Plane k of the item, with the rotation R = (k - z0) mod 9 fixed at
     // compile time.
-    template <int RQ>
+    template <int RQ, bool kLap>
     static __device__ __forceinline__ void plane_step(Walk &wk, R &rg, const float *ringA,
                                                       const float *ringB, const View &v,
                                                       const Coeffs &c, unsigned *status,
@@ -302,7 +308,7 @@ struct Kern {
         }
 
         const float gzk = wk.gzb[BI(0)];
-        float2 o[2];
+        float2 o[2], lp[2];
 #pragma unroll
         for (int p = 0; p < 2; ++p) {
             float2 s[5];
@@ -318,6 +324,7 @@ struct Kern {
             lap = fma2(splat(c.c3), fma2(splat(-6.0f), uc, s[3]), lap);
             lap = fma2(splat(c.c2), fma2(splat(-6.0f), uc, s[2]), lap);
             lap = fma2(splat(c.c1), fma2(splat(-6.0f), uc, s[1]), lap);
+            lp[p] = lap;
             const float2 gd = mul2(pair(wk.gxy, p), splat(gzk));
             const float2 ngd = mul2(pair(wk.gxy, p), splat(-gzk));   // -gd, exactly
             const float2 t = fma2(pair(wc, p), lap, fma2(splat(2.0f), uc, mul2(ngd, pair(upc, p))));
@@ -340,6 +347,17 @@ struct Kern {
             wk.out_k[0] = out.x;
             if (wk.nvalid > 1) wk.out_k[1] = out.y;
             if (wk.nvalid > 2) wk.out_k[2] = out.z;
+        }
+        if constexpr (kLap) {   // the stencil sum, for the adjoint's imaging
+            float *lk = wk.out_k + v.lap_delta;
+            const float4 l4 = make_float4(lp[0].x, lp[0].y, lp[1].x, lp[1].y);
+            if (wk.nvalid == 4) {
+                __stcs(reinterpret_cast<float4 *>(lk), l4);
+            } else if (wk.nvalid > 0) {
+                lk[0] = l4.x;
+                if (wk.nvalid > 1) lk[1] = l4.y;
+                if (wk.nvalid > 2) lk[2] = l4.z;
+            }
         }
         wk.out_k += v.g.plane;
         if (k == wk.rnext_k)
@@ -424,7 +442,8 @@ struct Kern {
             for (int kb = it.z0; kb < it.z1; kb += kUnroll) {
 #define WS_PLANE(RQ)                                                                         \
     if (kb + (RQ) >= it.z1) break;                                                           \
-    plane_step<RQ>(wk, rg, ringA, ringB, v, c, status, it, kb + (RQ), i, j, offA, offB);    \
+    plane_step<RQ, S::kStoreLap>(wk, rg, ringA, ringB, v, c, status, it, kb + (RQ), i, j, offA, \
+                                 offB);                                                     \
     if (!warp_all_ok(wk)) break;
                 WS_PLANE(0)
                 WS_PLANE(1)
@@ -497,13 +516,13 @@ __device__ __forceinline__ void stream_body(const S &src, const Coeffs &c, unsig
     }
 }
 
-template <int TX, int TY, int NA, int NB, int MINB>
+template <int TX, int TY, int NA, int NB, int MINB, bool kLap>
 __global__ void __launch_bounds__(StreamCfg<TX, TY, NA, NB>::kThreads, MINB)
     step_stream_kernel(const __grid_constant__ StreamMaps maps, float *__restrict__ up,
                        const __grid_constant__ StepArgs a, const int zb, const int tiles_x,
                        const int ntiles, const int nitems, const int *__restrict__ rec_ptr,
                        const RecEntry *__restrict__ rec) {
-    const OneGrid<TX, TY> src{maps, a, up, zb, tiles_x, ntiles, nitems, rec_ptr, rec};
+    const OneGrid<TX, TY, kLap> src{maps, a, up, zb, tiles_x, ntiles, nitems, rec_ptr, rec};
     stream_body<TX, TY, NA, NB>(src, a.c, a.status);
 }
 
@@ -532,11 +551,11 @@ cudaError_t occupancy(KernFn kern, int threads, size_t smem, int *ctas_per_sm, i
     return cudaSuccess;
 }
 
-template <int TX, int TY, int NA, int NB, int MINB>
-cudaError_t launch_tile(const StreamMaps &maps, float *up, const StepArgs &a, int zb,
-                        const int *rec_ptr, const RecEntry *rec, cudaStream_t s) {
+template <int TX, int TY, int NA, int NB, int MINB, bool kLap>
+cudaError_t launch_tile_as(const StreamMaps &maps, float *up, const StepArgs &a, int zb,
+                           const int *rec_ptr, const RecEntry *rec, cudaStream_t s) {
     using Cfg = StreamCfg<TX, TY, NA, NB>;
-    auto kern = step_stream_kernel<TX, TY, NA, NB, MINB>;
+    auto kern = step_stream_kernel<TX, TY, NA, NB, MINB, kLap>;
     static int ctas_per_sm = 0, sms = 0;
     cudaError_t e = occupancy(kern, Cfg::kThreads, Cfg::kSmem, &ctas_per_sm, &sms);
     if (e != cudaSuccess) return e;
@@ -550,13 +569,20 @@ cudaError_t launch_tile(const StreamMaps &maps, float *up, const StepArgs &a, in
 }
 
 template <int TX, int TY, int NA, int NB, int MINB>
+cudaError_t launch_tile(const StreamMaps &maps, float *up, const StepArgs &a, int zb,
+                        const int *rec_ptr, const RecEntry *rec, cudaStream_t s) {
+    if (a.lap) return launch_tile_as<TX, TY, NA, NB, MINB, true>(maps, up, a, zb, rec_ptr, rec, s);
+    return launch_tile_as<TX, TY, NA, NB, MINB, false>(maps, up, a, zb, rec_ptr, rec, s);
+}
+
+template <int TX, int TY, int NA, int NB, int MINB>
 cudaError_t slots_of(bool batch, int *slots) {
     using Cfg = StreamCfg<TX, TY, NA, NB>;
     static int c1 = 0, n1 = 0, c2 = 0, n2 = 0;
     cudaError_t e = batch ? occupancy(step_batch_kernel<TX, TY, NA, NB, MINB>, Cfg::kThreads,
                                       Cfg::kSmem, &c2, &n2)
-                          : occupancy(step_stream_kernel<TX, TY, NA, NB, MINB>, Cfg::kThreads,
-                                      Cfg::kSmem, &c1, &n1);
+                          : occupancy(step_stream_kernel<TX, TY, NA, NB, MINB, false>,
+                                      Cfg::kThreads, Cfg::kSmem, &c1, &n1);
     if (e == cudaSuccess) *slots = batch ? c2 * n2 : c1 * n1;
     return e;
 }
