@@ -120,12 +120,15 @@ struct ws_handle {
     bool tmap_ok = false;
     long long launches = 0;
 
-    // 16-bit storage (WS_STORAGE_BF16 / WS_STORAGE_FP16): the wavefields live
-    // in buf16 (buf then serves as FP32 scratch copies); the model stays in w.
+    // 16-bit storage (WS_STORAGE_BF16 / WS_STORAGE_FP16): the state lives in
+    // buf16[cur] (u^n) and d16 (u^n - u^{n-1}), the model in w16 as well as
+    // w; buf then serves as FP32 scratch copies.
     int storage = WS_STORAGE_FP32;
     uint16_t *buf16[2] = {nullptr, nullptr};
+    uint16_t *d16 = nullptr, *w16 = nullptr;
+    bool w16_ok = false;       // w16 holds the current model
     ws::Scale16 *scale = nullptr;
-    CUtensorMap t16_halo[2], t16_tile[2], t16_w;  // t16_w: FP32 model, 16-bit tile box
+    CUtensorMap t16_halo[2], t16_d, t16_w;
     double wmax = 0.0;         // max (V dt / h)^2 of the model
 
     // device scratch of ws_adjoint_gradient, kept for the next call
@@ -371,40 +374,33 @@ constexpr int kTile16X = 64, kTile16Y = 8;
 int encode_maps16(ws_t ws) {
     const ws::Geom &g = ws->g;
     int rc = WS_OK;
-    for (int b = 0; b < 2 && rc == WS_OK; ++b) {
+    for (int b = 0; b < 2 && rc == WS_OK; ++b)
         rc = encode_map(&ws->t16_halo[b], ws->buf16[b], g, kTile16X + 16, kTile16Y + 2 * ws::kHalo, 2);
-        if (rc == WS_OK) rc = encode_map(&ws->t16_tile[b], ws->buf16[b], g, kTile16X, kTile16Y, 2);
-    }
-    if (rc == WS_OK) rc = encode_map(&ws->t16_w, ws->w, g, kTile16X, kTile16Y, 4);
+    if (rc == WS_OK) rc = encode_map(&ws->t16_d, ws->d16, g, kTile16X, kTile16Y, 2);
+    if (rc == WS_OK) rc = encode_map(&ws->t16_w, ws->w16, g, kTile16X, kTile16Y, 2);
     return rc;
 }
 
-// FP32 buffers -> 16-bit buffers (both levels), exponent slots of the step.
+// FP32 buffers -> the 16-bit state (U = u^n, D = u^n - u^{n-1}), exponents
+// in the step's slot.
 int encode_state16(ws_t ws) {
-    const int sn = (int)(ws->step & 3), sp = (int)((ws->step + 3) & 3);
-    WS_CUDA(ws::launch_encode16(ws->storage, ws->buf[ws->cur], ws->buf16[ws->cur], ws->g, ws->scale,
-                                sn, ws->stream),
-            "encode field");
-    WS_CUDA(ws::launch_encode16(ws->storage, ws->buf[1 - ws->cur], ws->buf16[1 - ws->cur], ws->g,
-                                ws->scale, sp, ws->stream),
+    const int sn = (int)(ws->step & 3), so = (int)((ws->step + 1) & 3);
+    WS_CUDA(ws::launch_encode16(ws->storage, ws->buf[ws->cur], ws->buf[1 - ws->cur],
+                                ws->buf16[ws->cur], ws->d16, ws->g, ws->scale, sn, ws->stream),
             "encode field");
     // the next step accumulates max |u^{n+1}| into slot (step + 1) & 3
-    WS_CUDA(cudaMemsetAsync(&ws->scale->amax[(ws->step + 1) & 3], 0, sizeof(unsigned), ws->stream),
-            "encode field");
-    ws->launches += 4;
+    WS_CUDA(cudaMemsetAsync(&ws->scale->amax[so], 0, sizeof(unsigned), ws->stream), "encode field");
+    ws->launches += 2;
     return WS_OK;
 }
 
-// 16-bit buffers -> FP32 buffers (both levels).
+// The 16-bit state -> FP32 buffers (u^n, u^{n-1}).
 int decode_state16(ws_t ws) {
-    const int sn = (int)(ws->step & 3), sp = (int)((ws->step + 3) & 3);
-    WS_CUDA(ws::launch_decode16(ws->storage, ws->buf16[ws->cur], ws->buf[ws->cur], ws->g, ws->scale,
-                                sn, ws->stream),
+    const int sn = (int)(ws->step & 3);
+    WS_CUDA(ws::launch_decode16(ws->storage, ws->buf16[ws->cur], ws->d16, ws->buf[ws->cur],
+                                ws->buf[1 - ws->cur], ws->g, ws->scale, sn, ws->stream),
             "decode field");
-    WS_CUDA(ws::launch_decode16(ws->storage, ws->buf16[1 - ws->cur], ws->buf[1 - ws->cur], ws->g,
-                                ws->scale, sp, ws->stream),
-            "decode field");
-    ws->launches += 2;
+    ws->launches += 1;
     return WS_OK;
 }
 
@@ -494,6 +490,8 @@ void destroy(ws_t ws) {
     cudaFree(ws->energy);
     cudaFree(ws->buf16[0]);
     cudaFree(ws->buf16[1]);
+    cudaFree(ws->d16);
+    cudaFree(ws->w16);
     cudaFree(ws->scale);
     free_receivers(ws);
     delete ws->adj;
@@ -638,6 +636,7 @@ int ws_set_velocity(ws_t ws, const float *v, int on_device) {
                     cfl_limit());
     ws->wmax = c * c;
     ws->vel_ok = true;
+    ws->w16_ok = false;
     return WS_OK;
 }
 
@@ -667,6 +666,7 @@ int ws_set_slowness2(ws_t ws, const float *m, int on_device) {
                     cfl_limit());
     ws->wmax = c * c;
     ws->vel_ok = true;
+    ws->w16_ok = false;
     return WS_OK;
 }
 
@@ -749,11 +749,12 @@ int ws_set_storage(ws_t ws, int storage) {
     }
     if (storage != WS_STORAGE_FP32) {
         const size_t hb = size_t(ws->g.pnx) * ws->g.pny * ws->g.pnz * sizeof(uint16_t);
-        for (int b = 0; b < 2; ++b)
-            if (!ws->buf16[b]) {
-                WS_CUDA(cudaMalloc(&ws->buf16[b], hb), "cudaMalloc 16-bit field");
-                WS_CUDA(cudaMemsetAsync(ws->buf16[b], 0, hb, ws->stream), "zero 16-bit field");
+        for (uint16_t **f : {&ws->buf16[0], &ws->buf16[1], &ws->d16, &ws->w16})
+            if (!*f) {
+                WS_CUDA(cudaMalloc(f, hb), "cudaMalloc 16-bit field");
+                WS_CUDA(cudaMemsetAsync(*f, 0, hb, ws->stream), "zero 16-bit field");
             }
+        ws->w16_ok = false;
         if (!ws->scale) {
             WS_CUDA(cudaMalloc(&ws->scale, sizeof(ws::Scale16)), "cudaMalloc scales");
             WS_CUDA(cudaMemsetAsync(ws->scale, 0, sizeof(ws::Scale16), ws->stream), "zero scales");
@@ -812,6 +813,11 @@ int ws_step(ws_t ws, int nsteps) {
         tiling.zb = ws->tiling.zb > 0 ? ws->tiling.zb : default_zblock(ws->g.nz);
         int rc = build_rec_tiles(ws, tiling);
         if (rc != WS_OK) return rc;
+        if (!ws->w16_ok) {
+            WS_CUDA(ws::launch_model16(ws->w, ws->w16, ws->g, ws->stream), "16-bit model");
+            ws->launches++;
+            ws->w16_ok = true;
+        }
     } else {
         int rc = prepare_fp32(ws, &kern, &tiling);
         if (rc != WS_OK) return rc;
@@ -825,8 +831,8 @@ int ws_step(ws_t ws, int nsteps) {
             for (int q = 0; q < a.src.n; ++q)
                 hint = std::max(hint, std::fabs((double)a.src.s[q].amp) * ws->wmax);
             cudaError_t e = ws::launch_step_stream16(
-                ws->storage, &ws->t16_halo[ws->cur], &ws->t16_tile[1 - ws->cur], &ws->t16_w,
-                ws->buf16[1 - ws->cur], a, ws->scale, ws->step, (float)hint, tiling,
+                ws->storage, &ws->t16_halo[ws->cur], &ws->t16_d, &ws->t16_w,
+                ws->buf16[1 - ws->cur], ws->d16, a, ws->scale, ws->step, (float)hint, tiling,
                 ws->nrec > 0 ? ws->rec_ptr : nullptr, ws->rec_entries, ws->stream);
             ws->launches++;
             if (e != cudaSuccess) return cuda_fail(e, "ws_step launch");

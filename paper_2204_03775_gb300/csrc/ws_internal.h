@@ -150,28 +150,34 @@ cudaError_t launch_step_batch(const BatchShot *shots, const int2 *items, int nit
                               const Coeffs &c, unsigned *status, int tx, int ty, cudaStream_t s);
 
 // ---- 16-bit field storage (WS_STORAGE_BF16 / WS_STORAGE_FP16) ----
-// Ring of per-field power-of-two exponents and maxima, indexed by step & 3:
-// the field u^n is stored as u^n * 2^exps[n & 3]; amax[n & 3] = max |u^n|
-// (float bits, true units), accumulated by the step that writes u^n.
+// The state is U = u^n and D = u^n - u^{n-1}, 16 bits each; the model is
+// FP16 of (V dt/h)^2 * 2^kW16Exp. Ring of power-of-two exponents and maxima,
+// indexed by step & 3: U and D of step n are stored as u^n * 2^e[n&3] and
+// d^n * 2^e[n&3]; amax = max |u^n| (float bits, true units), accumulated by
+// the step that writes u^n.
+constexpr int kW16Exp = 12;
 struct Scale16 {
-    int exps[4];
+    int e[4];
     unsigned amax[4];
 };
 bool stream16_tiling_supported(int tx, int ty);
-// tmap_u: u^n (16-bit) with box (tx+16, ty+8, 1); tmap_up: u^{n-1} (16-bit)
-// and tmap_w: (V dt/h)^2 (FP32), both with box (tx, ty, 1). src_hint: bound
-// on |(V dt)^2 s(t_n)| of this step's sources (picks the output exponent
-// while the field is still zero).
-cudaError_t launch_step_stream16(int storage, const CUtensorMap *tmap_u, const CUtensorMap *tmap_up,
-                                 const CUtensorMap *tmap_w, uint16_t *up, const StepArgs &a,
-                                 Scale16 *sc, long long step, float src_hint,
+// tmap_u: U (16-bit) with box (tx+16, ty+8, 1); tmap_d: D and tmap_w: the
+// 16-bit model, both with box (tx, ty, 1). u_out receives U' (the other U
+// buffer); D is updated in place at d_io. src_hint: bound on
+// |(V dt)^2 s(t_n)| of this step's sources (picks the output exponents while
+// the field is still zero).
+cudaError_t launch_step_stream16(int storage, const CUtensorMap *tmap_u, const CUtensorMap *tmap_d,
+                                 const CUtensorMap *tmap_w, uint16_t *u_out, uint16_t *d_io,
+                                 const StepArgs &a, Scale16 *sc, long long step, float src_hint,
                                  const StreamTiling &t, const int *rec_ptr, const RecEntry *rec,
                                  cudaStream_t s);
-// FP32 padded field <-> 16-bit padded field (interior), exponent slot `slot`.
-cudaError_t launch_encode16(int storage, const float *f, uint16_t *out, const Geom &g, Scale16 *sc,
-                            int slot, cudaStream_t s);
-cudaError_t launch_decode16(int storage, const uint16_t *in, float *f, const Geom &g,
-                            const Scale16 *sc, int slot, cudaStream_t s);
+// FP32 padded (u^n, u^{n-1}) <-> 16-bit padded (U, D) (interior), exponent slot `slot`.
+cudaError_t launch_encode16(int storage, const float *u, const float *up, uint16_t *U, uint16_t *D,
+                            const Geom &g, Scale16 *sc, int slot, cudaStream_t s);
+cudaError_t launch_decode16(int storage, const uint16_t *U, const uint16_t *D, float *u, float *up,
+                            const Geom &g, const Scale16 *sc, int slot, cudaStream_t s);
+// (V dt/h)^2 (FP32 padded) -> the 16-bit model.
+cudaError_t launch_model16(const float *w, uint16_t *w16, const Geom &g, cudaStream_t s);
 
 // ---- adjoint gradient ----
 int residual_partial_count();

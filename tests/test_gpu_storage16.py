@@ -1,13 +1,15 @@
 """16-bit field storage (ws_set_storage): exactness of one step, stated accuracy.
 
-1. One step, bit for bit: from a state whose values are exact in the 16-bit
-   format, with a model whose (V dt/h)^2 is exact in FP32, the 16-bit kernel
-   must store exactly the FP32 kernel's result rounded to 16 bits (to nearest
-   even), and record exactly the FP32 kernel's traces: it computes the same
-   FP32 operations on exactly power-of-two-scaled numbers.
+The 16-bit modes store U = u^n and D = u^n - u^{n-1} (velocity form) and the
+model (V dt/h)^2 in FP16.
+1. One step, bit for bit: from a state whose u^n and u^n - u^{n-1} are exact
+   in the 16-bit format, with a model exact in FP16, the 16-bit kernel must
+   store exactly U' = round16(u^{n+1}) and D' = round16(u^{n+1} - u^n) of the
+   FP32 kernel's u^{n+1}, and record exactly the FP32 kernel's traces: it
+   computes the same FP32 operations on exactly power-of-two-scaled numbers.
 2. Accuracy against the FP64 oracle over many steps, checked against the
-   bounds stated in the header and the design notes (rounding the two stored
-   levels to 16 bits each step dominates; FP32 storage stays near 1e-6).
+   bounds stated in the header and the design notes (the rounding of U' each
+   step dominates; FP32 storage stays near 1e-6).
 3. Converting FP32 -> 16-bit -> FP32 keeps the state within one 16-bit rounding.
 """
 
@@ -49,10 +51,13 @@ def test_one_step_equals_rounded_fp32(storage, name):
     dt = 0.25 * h / v                      # (V dt / h)^2 = 1/16, exact everywhere
     vel = np.full((nz, ny, nx), v, np.float32)
     rng = np.random.default_rng(4)
-    # values in +-[0.5, 1): one binade, so rounding is scale-independent
-    mag = rng.uniform(0.5, 1.0, (2, nz, ny, nx)) * rng.choice([-1.0, 1.0], (2, nz, ny, nx))
-    u0 = ROUND[name](mag[0].astype(np.float32))
-    um1 = ROUND[name](mag[1].astype(np.float32))
+    # u^n and d = u^n - u^{n-1} on a coarse grid (multiples of 2^-7 in +-[0.5, 1)
+    # and +-[2^-3, 2^-2)): exact in BF16 and FP16, and u^{n-1} = u^n - d exact in FP32
+    sgn = lambda: rng.choice([-1.0, 1.0], (nz, ny, nx))
+    u0 = (np.round(rng.uniform(0.5, 1.0, (nz, ny, nx)) * 128) / 128 * sgn()).astype(np.float32)
+    d0 = (np.round(rng.uniform(0.125, 0.25, (nz, ny, nx)) * 128) / 128 * sgn()).astype(np.float32)
+    assert np.array_equal(ROUND[name](u0), u0) and np.array_equal(ROUND[name](d0), d0)
+    um1 = (u0 - d0).astype(np.float32)
     rec = np.array([[5, 5, 5], [60, 20, 15], [95, 39, 29]], np.int32)
 
     def one_step(st):
@@ -70,27 +75,29 @@ def test_one_step_equals_rounded_fp32(storage, name):
         u, up = wsb.ws_read_field(hd)
         return u, up, wsb.ws_read_traces(hd)
 
-    u32, up32, tr32 = one_step(None)
+    u32, _, tr32 = one_step(None)
     u16, up16, tr16 = one_step(storage)
-    np.testing.assert_array_equal(up16, u0)                 # u^n kept exactly
     np.testing.assert_array_equal(tr16, tr32)               # traces: the FP32 values
-    # u^{n+1}: the FP32 result rounded to 16 bits. The kernel rounds x * 2^e
-    # with the field's maximum near 2^12, so FP16 values stay normal down to
-    # |x| ~ 2^-26 while x itself rounds subnormally below 2^-14: compare
-    # exactly where both are normal, and within the normal spacing below.
-    ref = ROUND[name](u32)
+    ref_u = ROUND[name](u32)
+    ref_d = ROUND[name]((u32 - u0).astype(np.float32))
     if name == "bf16":   # BF16 has the FP32 exponent range: rounding is scale-free
-        np.testing.assert_array_equal(u16, ref)
+        np.testing.assert_array_equal(u16, ref_u)
+        np.testing.assert_array_equal(up16, (ref_u - ref_d).astype(np.float32))
         return
-    big = np.abs(u32) >= 2.0 ** -13
-    assert big.mean() > 0.99
-    np.testing.assert_array_equal(u16[big], ref[big])
-    assert np.abs(u16[~big] - u32[~big]).max(initial=0.0) <= 2.0 ** -24
+    # FP16: the kernel rounds x * 2^e with the field's maximum near 2^12, so
+    # values stay normal down to |x| ~ 2^-26 while x itself rounds subnormally
+    # below 2^-14: compare exactly where both are normal
+    nu = np.abs(u32) >= 2.0 ** -13
+    nd = nu & (np.abs(u32 - u0) >= 2.0 ** -13)
+    assert nd.mean() > 0.99
+    np.testing.assert_array_equal(u16[nu], ref_u[nu])
+    np.testing.assert_array_equal(up16[nd], (ref_u - ref_d).astype(np.float32)[nd])
+    assert np.abs(u16[~nu] - u32[~nu]).max(initial=0.0) <= 2.0 ** -23
 
 
 # stated accuracy (relative L2 vs the FP64 oracle) after 200 steps on the
 # layered survey; FP32 storage is there for contrast
-BOUNDS = {"fp32": 1e-5, "fp16": 6e-3, "bf16": 5e-2}
+BOUNDS = {"fp32": 1e-5, "fp16": 3e-3, "bf16": 2.5e-2}
 
 
 @pytest.mark.parametrize("storage,name", [(wsb.WS_STORAGE_FP32, "fp32")] + MODES)
