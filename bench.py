@@ -34,7 +34,7 @@ BYTES_PER_POINT = 16  # read u^n, u^{n-1}, (V dt/h)^2; write u^{n+1} (FP32)
 FALLBACK_HBM_GBS = 6800.0
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "step_stream_layered1024_ncu.txt")
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_2204_03775_gb300", "csrc", f)
-                  for f in ("ws_kernels_stream.cu", "ws_internal.h")]
+                  for f in ("ws_kernels_stream.cu", "ws_ptx.cuh", "ws_internal.h")]
 
 
 def parse_args():
@@ -49,6 +49,13 @@ def parse_args():
     ap.add_argument("--zblock", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--case", choices=["survey", "fp16", "bf16", "adjoint", "batched"],
+                    default="survey",
+                    help="survey (default): the JSON line. The others run one workload alone "
+                         "(for profilers) and print its timing: fp16/bf16 = the layered survey "
+                         "of --size with 16-bit storage for --warmup + --steps steps; adjoint = "
+                         "one shot of the adjoint survey (--size, --steps) gradient, three "
+                         "times; batched = the 64-shot batch for --steps steps")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the 64-shot batched-launch report")
     ap.add_argument("--no-adjoint", action="store_true",
@@ -383,6 +390,65 @@ def adjoint_report():
             "timing": "host clock, 16 shots one after another"}
 
 
+def run_case(args):
+    """One workload alone, for profiler runs (see --case)."""
+    import numpy as np
+    import torch
+    import paper_2204_03775_gb300 as wsb
+    from paper_2204_03775_gb300 import synthetic
+
+    wsb.load_library(build_if_missing=True)
+    n, K, W = args.size, args.steps, args.warmup
+    t0 = time.perf_counter()
+    if args.case in ("fp16", "bf16"):
+        w = synthetic.layered_survey(n, n, n, nt=K + W)
+        h = wsb.ws_create(w.nx, w.ny, w.nz, w.h, w.dt)
+        wsb.ws_set_storage(h, wsb.WS_STORAGE_FP16 if args.case == "fp16" else wsb.WS_STORAGE_BF16)
+        wsb.ws_set_velocity(h, w.vel)
+        wsb.ws_set_sponge(h, *w.sponge)
+        for s in w.sources:
+            wsb.ws_add_source(h, *s)
+        wsb.ws_set_receivers(h, w.receivers, K + W)
+        wsb.ws_step(h, W)
+        wsb.ws_synchronize(h)
+        t0 = time.perf_counter()
+        wsb.ws_step(h, K)
+        wsb.ws_synchronize(h)
+        cells = w.points * K
+    elif args.case == "adjoint":
+        w = synthetic.adjoint_survey(n, K)
+        m0 = torch.from_numpy((1.0 / w.vel_start.astype(np.float64) ** 2).astype(np.float32)).cuda()
+        h = wsb.ws_create(w.nx, w.ny, w.nz, w.h, w.dt)
+        wsb.ws_set_sponge(h, *w.sponge)
+        for s in w.shots[0]:
+            wsb.ws_add_source(h, *s)
+        wsb.ws_set_receivers(h, w.receivers, w.nt)
+        wsb.ws_set_slowness2(h, m0)
+        wsb.ws_autotune(h)
+        d = torch.zeros((len(w.receivers), w.nt), dtype=torch.float32, device="cuda")
+        g = torch.empty_like(m0)
+        for rep in range(3):
+            if rep == 1:
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+            wsb.ws_adjoint_gradient(h, d, wsb.WS_ADJ_DATA, g)
+        torch.cuda.synchronize()
+        cells = 2 * w.nx * w.ny * w.nz * w.nt   # two gradients timed, one forward-run of cells each
+    else:
+        shots = synthetic.batched_shots(nt=K)
+        hs = [_shot_handle(wsb, x, K + 60) for x in shots]
+        b = wsb.ws_batch_create(hs)
+        wsb.ws_batch_step(b, 60)
+        wsb.ws_batch_synchronize(b)
+        t0 = time.perf_counter()
+        wsb.ws_batch_step(b, K)
+        wsb.ws_batch_synchronize(b)
+        cells = sum(x.points for x in shots) * K
+    el = time.perf_counter() - t0
+    print(json.dumps({"case": args.case, "size": n, "steps": K, "seconds": el,
+                      "Gpoint_updates_per_s": cells / el / 1e9}), flush=True)
+
+
 def run_reference(args):
     """The oracle as it stands, timed on the host cores (rank 0 only)."""
     world, rank, _ = dist_setup(args.gpus)
@@ -431,6 +497,8 @@ def main():
         raise SystemExit("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.case != "survey":
+        return run_case(args)
 
     import numpy as np
     import torch
