@@ -308,6 +308,17 @@ long long ws_batch_launch_count(ws_batch_t b);
  * last call (TIMEOUT when a bounded wait in a kernel ran out). Clears it. */
 int ws_synchronize(ws_t ws);
 
+/* Test hook for the failure path (the paper has no counterpart): the next
+ * ws_step that uses the streaming FP32 kernel withholds the first copy of
+ * work item `item` (items are numbered z block by z block, then by tile),
+ * so the bounded waits of the CTA that owns it give up after about one
+ * second. That step's result is then invalid: ws_synchronize returns
+ * TIMEOUT, and the caller must write a new state (ws_write_field) before
+ * stepping on; the handle and the CUDA context stay usable. item = -1
+ * clears a pending stall. No GPU fault is involved: the kernel only stops
+ * waiting, records the status and drains its own copies. */
+int ws_test_stall(ws_t ws, int item);
+
 /* Number of kernel launches issued by this handle since creation. */
 long long ws_launch_count(ws_t ws);
 

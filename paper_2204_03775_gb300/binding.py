@@ -88,6 +88,7 @@ def load_library(build_if_missing: bool = False):
         "ws_energy_noalloc": (i, [vp, vp, vp, i, i, i, d, d, vp, vp]),
         "ws_last_error": (ctypes.c_char_p, []),
         "ws_autotune": (i, [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]),
+        "ws_test_stall": (i, [vp, i]),
         "ws_batch_create": (i, [ctypes.POINTER(vp), i, vp]),
         "ws_batch_destroy": (i, [vp]),
         "ws_batch_set_tiling": (i, [vp, i, i, i]),
@@ -356,6 +357,11 @@ def ws_batch_synchronize(b: Batch) -> None:
 
 def ws_batch_launch_count(b: Batch) -> int:
     return int(load_library().ws_batch_launch_count(b.ptr))
+
+
+def ws_test_stall(ws: Handle, item: int) -> None:
+    """Test hook: the next streaming step withholds one copy of work item `item` (see header)."""
+    _check(load_library().ws_test_stall(ws.ptr, int(item)), "ws_test_stall")
 
 
 def ws_launch_count(ws: Handle) -> int:

@@ -133,6 +133,7 @@ struct ws_handle {
 
     // device scratch of ws_adjoint_gradient, kept for the next call
     struct AdjointCache *adj = nullptr;
+    int stall_item = -1;       // test hook (ws_test_stall), consumed by the next FP32 step
 };
 
 // A group of handles advanced together: one persistent launch per step
@@ -419,6 +420,7 @@ void sources_of_step(const ws_t ws, long long n, ws::Sources *out) {
 // Step arguments common to every step of the handle's model.
 ws::StepArgs base_args(const ws_t ws) {
     ws::StepArgs a{};
+    a.stall_item = -1;
     a.g = ws->g;
     a.c.c1 = (float)kW1;
     a.c.c2 = (float)kW2;
@@ -838,9 +840,12 @@ int ws_step(ws_t ws, int nsteps) {
             if (e != cudaSuccess) return cuda_fail(e, "ws_step launch");
         } else {
             const int c = ws->cur;
+            a.stall_item = kern == WS_KERNEL_STREAM ? ws->stall_item : -1;
+            ws->stall_item = -1;
             int rc = step_fp32(ws, a, kern, tiling, ws->buf[c], &ws->tmap_halo[c], ws->buf[1 - c],
                                &ws->tmap_tile[1 - c], ws->buf[1 - c], ws->step, true,
                                ws->nrec > 0);
+            a.stall_item = -1;
             if (rc != WS_OK) return rc;
         }
         ws->cur = 1 - ws->cur;
@@ -1580,6 +1585,13 @@ int ws_batch_synchronize(ws_batch_t b) {
 }
 
 long long ws_batch_launch_count(ws_batch_t b) { return b ? b->launches : -1; }
+
+int ws_test_stall(ws_t ws, int item) {
+    if (!ws) return fail(WS_ERR_BADARG, "ws_test_stall: NULL handle");
+    if (item < -1) return fail(WS_ERR_BADARG, "ws_test_stall: item must be >= -1");
+    ws->stall_item = item;
+    return WS_OK;
+}
 
 long long ws_launch_count(ws_t ws) { return ws ? ws->launches : -1; }
 

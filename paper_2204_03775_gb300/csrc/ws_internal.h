@@ -94,6 +94,7 @@ struct StepArgs {
     long long trace_step;        // column of this step in traces
     unsigned *status;            // device status word
     float *lap;                  // if not null: receives the stencil sum L u^n (padded field)
+    int stall_item;              // test hook: withhold the first copy of this work item (-1: none)
 };
 
 // Launchers (stream-ordered, no synchronization).

@@ -77,10 +77,12 @@ struct StreamMaps {
     CUtensorMap u, up, w;
 };
 
-// What the producer needs of an item: its extent and the three maps.
+// What the producer needs of an item: its extent and the three maps;
+// stall (a test hook) withholds the item's first copy.
 struct Job {
     Item it;
     const CUtensorMap *u, *up, *w;
+    bool stall;
 };
 
 // What the consumers need of an item's grid.
@@ -112,7 +114,8 @@ struct OneGrid {
 
     __device__ __forceinline__ int nitems() const { return n; }
     __device__ __forceinline__ Job job(int item) const {
-        return Job{item_of(item, tiles_x, ntiles, zb, a.g.nz, TX, TY), &mp.u, &mp.up, &mp.w};
+        return Job{item_of(item, tiles_x, ntiles, zb, a.g.nz, TX, TY), &mp.u, &mp.up, &mp.w,
+                   item == a.stall_item};
     }
     __device__ __forceinline__ Item view(int item, View *v) const {
         v->g = a.g;
@@ -147,7 +150,7 @@ struct ShotBatch {
         const BatchShot &s = shots[e.x];
         const int p = s.cur0 ^ (t & 1);
         return Job{item_of(e.y, s.tiles_x, s.ntiles, s.zb, s.g.nz, TX, TY), &s.halo[p],
-                   &s.tile[1 - p], &s.w};
+                   &s.tile[1 - p], &s.w, false};
     }
     __device__ __forceinline__ Item view(int item, View *v) const {
         const int2 e = items[item];
@@ -230,8 +233,13 @@ struct Kern {
         for (int item = blockIdx.x; item < src.nitems(); item += gridDim.x) {
             const Job jb = src.job(item);
             const int nb = jb.it.z1 - jb.it.z0, nplanes = nb + 2 * kHalo;
-            for (int pr = 0; pr < 2 * kHalo; ++pr)
+            for (int pr = 0; pr < 2 * kHalo; ++pr) {
+                if (pr == 0 && jb.stall) {   // never filled: the consumers' bounded waits run out
+                    ++gA;
+                    continue;
+                }
                 if (!produce_a(rg, ringA, jb, gA++, pr, status)) return;
+            }
             for (int b = 0; b < nb; ++b) {
                 if (!produce_b(rg, ringB, jb, gB++, b, status)) return;
                 if (b + 2 * kHalo < nplanes && !produce_a(rg, ringA, jb, gA++, b + 2 * kHalo, status))
