@@ -161,6 +161,21 @@ def dist_setup(n_gpus):
     return world, rank, local
 
 
+def max_over_ranks(x: float, dist, device) -> float:
+    """The largest x over all ranks (x itself without a process group)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, points: int, steps: int, seconds: float) -> float:
+    """Point updates per second of all replicas together (each rank did points x steps)."""
+    return world * points * steps / seconds / 1e9
+
+
 def cpu_baseline(w, target_s=15.0):
     """The FP64 oracle on a bounded slab of the same survey (host cores)."""
     import numpy as np
@@ -554,9 +569,7 @@ def main():
     elapsed = evs[0].elapsed_time(evs[K]) / 1e3
     per_launch = [evs[s].elapsed_time(evs[s + 1]) / 1e3 for s in range(K)]
     if dist is not None:
-        t = torch.tensor([elapsed], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
+        elapsed = max_over_ranks(elapsed, dist, "cuda")
 
     # end to end through the public API from pinned host memory: upload the
     # model, run the K steps, read the traces back
@@ -575,10 +588,8 @@ def main():
         wsb.ws_read_traces(h, traces)
         e2e_s = time.perf_counter() - t0
         if dist is not None:
-            t = torch.tensor([e2e_s], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
-        e2e = {"value": world * npts * K / e2e_s / 1e9, "unit": UNIT,
+            e2e_s = max_over_ranks(e2e_s, dist, "cuda")
+        e2e = {"value": whole_job_rate(world, npts, K, e2e_s), "unit": UNIT,
                "h2d_bytes_per_step": vel_pinned.numel() * 4 / K,
                "d2h_bytes_per_step": traces.numel() * 4 / K,
                "what": "ws_set_velocity (pinned host model) + ws_step(K) + ws_read_traces (pinned host)"}
@@ -591,7 +602,7 @@ def main():
     avg_launch = statistics.mean(per_launch)
     peak, peak_kind = measured_peak()
     achieved = BYTES_PER_POINT * npts / avg_launch / 1e9
-    value = world * npts * K / elapsed / 1e9
+    value = whole_job_rate(world, npts, K, elapsed)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": 1e3 * elapsed / K, "higher_is_better": True, "scaling": "weak",
