@@ -182,18 +182,27 @@ def cpu_baseline(w, target_s=15.0):
     import oracle
 
     oracle.build()
-    # calibrate on two steps of a 4-plane slab, then size the sample to ~target_s
-    t0 = time.perf_counter()
-    oracle.run(w.vel[:4], w.h, w.dt, 2, sponge=w.sponge, window=(0, 0, 0, w.nx, w.ny, w.nz))
-    rate = 2 * 4 * w.nx * w.ny / (time.perf_counter() - t0)
     depth = int(min(w.nz, max(w.sources[0][2] + 5, 32)))
-    steps = int(max(2, min(400, target_s * rate / (depth * w.nx * w.ny))))
     slab = np.ascontiguousarray(w.vel[:depth])
+    win = (0, 0, 0, w.nx, w.ny, w.nz)
+    cells = depth * w.nx * w.ny
+    # calibrate on the slab itself (the first call also starts the thread pool),
+    # then size the timed sample to about target_s seconds
+    oracle.run(slab, w.h, w.dt, 1, sources=w.sources, sponge=w.sponge, window=win)
+    n = 3
+    while True:
+        t0 = time.perf_counter()
+        oracle.run(slab, w.h, w.dt, n, sources=w.sources, sponge=w.sponge, window=win)
+        el = time.perf_counter() - t0
+        if el > 1.0 or n >= 400:
+            break
+        n *= 4
+    steps = int(max(3, min(4000, target_s * n / el)))
     t0 = time.perf_counter()
     oracle.run(slab, w.h, w.dt, steps, sources=w.sources, receivers=None, sponge=w.sponge,
-               window=(0, 0, 0, w.nx, w.ny, w.nz))
+               window=win)
     el = time.perf_counter() - t0
-    pts = depth * w.nx * w.ny * steps
+    pts = cells * steps
     return {"value": pts / el / 1e9, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
             "sample": f"FP64 oracle, top slab k in [0,{depth}) of the {w.nx}x{w.ny}x{w.nz} "
                       f"survey (same model, taper, source), {steps} steps from rest, "

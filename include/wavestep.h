@@ -213,7 +213,7 @@ int ws_energy_noalloc(const float *u, const float *u_prev, const float *v, int n
  * imaging: two forward passes and one backward pass in all.
  *
  * Needs a velocity model, receivers and FP32 storage, else STATE. Device
- * scratch: about 3 sqrt(N) + 4 padded fields, 12 bytes per cell and two
+ * scratch: about 3 sqrt(N) + 6 padded fields and two
  * trace arrays, allocated by the first call and kept by the handle for the
  * next ones while N, the receiver count and the tiling stay the same (freed
  * by ws_destroy).

@@ -179,7 +179,8 @@ struct AdjointCache {
     std::vector<float *> ck;
     std::vector<float *> lap;       // L u^n of the segment's steps
     MappedField ring[2], rho[2];    // recomputed u^n / u^{n-1}; rho^{k+1} / rho^{k+2}
-    double *acc = nullptr, *partials = nullptr;
+    float2 *acc = nullptr;          // compensated FP32 gradient sums, padded layout
+    double *partials = nullptr;
     float *r = nullptr, *dd = nullptr, *grad = nullptr;
     int *rec = nullptr;
     ~AdjointCache() {
@@ -1029,7 +1030,7 @@ int ws_adjoint_gradient(ws_t ws, const float *data, int mode, float *grad_m, dou
             if (r3 == WS_OK) r3 = field(&f);
         for (auto &f : ac->rho)
             if (r3 == WS_OK) r3 = field(&f);
-        if (r3 == WS_OK) e = grab(&ac->acc, 2 * fb);   // FP64, padded layout
+        if (r3 == WS_OK) e = grab(&ac->acc, 2 * fb);   // float2 per cell, padded layout
         if (r3 == WS_OK && e == cudaSuccess) e = grab(&ac->partials, sizeof(double) * (ws::residual_partial_count() + 1));
         if (r3 == WS_OK && e == cudaSuccess) e = grab(&ac->r, sizeof(float) * ntr);
         if (r3 == WS_OK && e == cudaSuccess) e = grab(&ac->dd, sizeof(float) * ntr);
@@ -1052,7 +1053,8 @@ int ws_adjoint_gradient(ws_t ws, const float *data, int mode, float *grad_m, dou
     std::vector<float *> &lap = ac->lap;
     MappedField *ring = ac->ring;
     MappedField *rho = ac->rho;
-    double *acc = ac->acc, *partials = ac->partials;
+    float2 *acc = ac->acc;
+    double *partials = ac->partials;
     float *r = ac->r, *grad = on_device ? grad_m : ac->grad;
     const float *d = data;
     int *rec = ac->rec;

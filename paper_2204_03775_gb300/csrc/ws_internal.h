@@ -191,13 +191,14 @@ cudaError_t launch_residual(const float *traces, const float *d_obs, long long n
 cudaError_t launch_inject(float *rho, const float *w, const float *gx, const float *gy,
                           const float *gz, const Geom &g, const int *rec_ijk, int nrec,
                           const float *r, int nt, int col, cudaStream_t s);
-// acc (FP64, padded layout) += rho * lapu (the stencil sum L u^n a step
-// stored), plus rho * amp / G at source cells.
+// acc (compensated FP32 {sum, correction} per cell, padded layout) +=
+// rho * lapu (the stencil sum L u^n a step stored), plus rho * amp / G at
+// source cells.
 cudaError_t launch_imaging(const float *rho, const float *lapu, const Geom &g, const Sources &src,
-                           const float *gx, const float *gy, const float *gz, double *acc,
+                           const float *gx, const float *gy, const float *gz, float2 *acc,
                            cudaStream_t s);
-// grad (unpadded float) = -V^2 acc (padded), V^2 = W (h / dt)^2.
-cudaError_t launch_finalize_gradient(const double *acc, const float *w, const Geom &g,
+// grad (unpadded float) = -V^2 (sum - correction) of acc, V^2 = W (h / dt)^2.
+cudaError_t launch_finalize_gradient(const float2 *acc, const float *w, const Geom &g,
                                      double h_over_dt2, float *grad, cudaStream_t s);
 
 // Discrete energy (FP64): partial sums per (row block, plane) into

@@ -78,16 +78,26 @@ __global__ void inject_kernel(float *__restrict__ rho, const float *__restrict__
 
 // acc += rho * (L u) with L u the stencil sum the step kernel stored while
 // recomputing u^{n+1} (the same float value the step used), and at source
-// cells rho * (h^2 s_n) / G. acc is FP64 in the padded layout, so a
-// thread's 4 consecutive x cells are one float4 of rho and of L u and two
-// double2 of acc. A block covers 128 x 8 cells of one plane; one thread
-// finds the block's sources first.
+// cells rho * (h^2 s_n) / G. The accumulator is a compensated FP32 sum
+// (Kahan): per cell a float2 {sum, correction} in the padded layout, so a
+// thread's 4 consecutive x cells are one float4 of rho, one of L u and two
+// of acc. GB300 runs FP64 at a small fraction of FP32, which made an FP64
+// accumulator the bottleneck of this pass; the compensated sum keeps the
+// rounding of 800 additions at the level of one. A block covers 128 x 8
+// cells of one plane; one thread finds the block's sources first.
+__device__ __forceinline__ void kahan_add(float &sum, float &corr, float x) {
+    const float y = x - corr;
+    const float t = sum + y;
+    corr = (t - sum) - y;
+    sum = t;
+}
+
 __global__ void __launch_bounds__(256) imaging_kernel(const float *__restrict__ rho,
                                                       const float *__restrict__ lapu, Geom g,
                                                       Sources src, const float *__restrict__ gx,
                                                       const float *__restrict__ gy,
                                                       const float *__restrict__ gz,
-                                                      double *__restrict__ acc) {
+                                                      float2 *__restrict__ acc) {
     const int i = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const int k = blockIdx.z;
@@ -108,35 +118,36 @@ __global__ void __launch_bounds__(256) imaging_kernel(const float *__restrict__ 
     const long long p = pidx(g, i, j, k);   // a multiple of 4: rows start on 32-cell lines
     const float4 r4 = *reinterpret_cast<const float4 *>(rho + p);
     const float4 l4 = __ldcs(reinterpret_cast<const float4 *>(lapu + p));
-    double2 a01 = *reinterpret_cast<const double2 *>(acc + p);
-    double2 a23 = *reinterpret_cast<const double2 *>(acc + p + 2);
-    double t[4] = {(double)r4.x * (double)l4.x, (double)r4.y * (double)l4.y,
-                   (double)r4.z * (double)l4.z, (double)r4.w * (double)l4.w};
+    float4 a01 = *reinterpret_cast<const float4 *>(acc + p);       // {s0, c0, s1, c1}
+    float4 a23 = *reinterpret_cast<const float4 *>(acc + p + 2);   // {s2, c2, s3, c3}
+    float t[4] = {r4.x * l4.x, r4.y * l4.y, r4.z * l4.z, r4.w * l4.w};
     const float rv[4] = {r4.x, r4.y, r4.z, r4.w};
     for (unsigned m = mask; m; m &= m - 1) {
         const SourceSample &ss = src.s[__ffs(m) - 1];
         const int l = ss.i - i;
         if (ss.j == j && l >= 0 && l < 4)
-            t[l] += (double)rv[l] * (double)ss.amp / ((double)gx[ss.i] * gy[j] * gz[k]);
+            t[l] = fmaf(rv[l], ss.amp / (gx[ss.i] * gy[j] * gz[k]), t[l]);
     }
     // cells past nx (x padding: zero in rho and in L u) accumulate zeros
-    a01.x += t[0];
-    a01.y += t[1];
-    a23.x += t[2];
-    a23.y += t[3];
-    *reinterpret_cast<double2 *>(acc + p) = a01;
-    *reinterpret_cast<double2 *>(acc + p + 2) = a23;
+    kahan_add(a01.x, a01.y, t[0]);
+    kahan_add(a01.z, a01.w, t[1]);
+    kahan_add(a23.x, a23.y, t[2]);
+    kahan_add(a23.z, a23.w, t[3]);
+    *reinterpret_cast<float4 *>(acc + p) = a01;
+    *reinterpret_cast<float4 *>(acc + p + 2) = a23;
 }
 
-// grad_m = -V^2 acc, V^2 = W (h/dt)^2; acc padded, unpadded float output.
-__global__ void finalize_kernel(const double *__restrict__ acc, const float *__restrict__ w,
+// grad_m = -V^2 (sum - correction), V^2 = W (h/dt)^2; acc padded, unpadded
+// float output.
+__global__ void finalize_kernel(const float2 *__restrict__ acc, const float *__restrict__ w,
                                 Geom g, double h_over_dt2, float *__restrict__ grad) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y, k = blockIdx.z;
     if (i >= g.nx) return;
     const long long o = ((long long)k * g.ny + j) * g.nx + i;
     const long long p = pidx(g, i, j, k);
-    grad[o] = (float)(-(double)w[p] * h_over_dt2 * acc[p]);
+    const float2 a = acc[p];
+    grad[o] = -w[p] * (float)h_over_dt2 * (a.x - a.y);
 }
 
 }  // namespace
@@ -162,7 +173,7 @@ cudaError_t launch_inject(float *rho, const float *w, const float *gx, const flo
 }
 
 cudaError_t launch_imaging(const float *rho, const float *lapu, const Geom &g, const Sources &src,
-                           const float *gx, const float *gy, const float *gz, double *acc,
+                           const float *gx, const float *gy, const float *gz, float2 *acc,
                            cudaStream_t s) {
     dim3 block(32, 8, 1);
     dim3 grid((g.nx + 127) / 128, (g.ny + 7) / 8, g.nz);
@@ -170,7 +181,7 @@ cudaError_t launch_imaging(const float *rho, const float *lapu, const Geom &g, c
     return cudaGetLastError();
 }
 
-cudaError_t launch_finalize_gradient(const double *acc, const float *w, const Geom &g,
+cudaError_t launch_finalize_gradient(const float2 *acc, const float *w, const Geom &g,
                                      double h_over_dt2, float *grad, cudaStream_t s) {
     dim3 grid((g.nx + 127) / 128, g.ny, g.nz);
     finalize_kernel<<<grid, 128, 0, s>>>(acc, w, g, h_over_dt2, grad);
