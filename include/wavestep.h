@@ -243,7 +243,7 @@ int ws_set_storage(ws_t ws, int storage);
 /* Choose the step kernel (WS_KERNEL_*) and, for WS_KERNEL_STREAM, its tile:
  * tile_x x tile_y in {32x8, 32x16, 64x8, 64x16, 64x32} (0, 0 = keep the
  * current tile; the default is 64x8), zblock >= 1 planes per work item
- * (0 = default, about 340). WS_KERNEL_STREAM needs nx >= tile_x and ny >= tile_y;
+ * (0 = default: about 200 planes, fewer on small grids). WS_KERNEL_STREAM needs nx >= tile_x and ny >= tile_y;
  * else BADARG. */
 int ws_set_kernel(ws_t ws, int kernel, int tile_x, int tile_y, int zblock);
 

@@ -229,10 +229,11 @@ bool stream_fits(const ws_t ws, const ws::StreamTiling &t) {
 }
 
 // Planes per work item: long blocks re-read fewer 4-plane halos at their
-// ends, but need enough items to keep every CTA busy; about 340 planes
-// measured best on the 1024^3 survey (three blocks).
+// ends, short ones give the in-order dispatch more, smaller items; about 200
+// planes measured best on the 1024^3 survey (five blocks of 205: 389.6
+// Gcell/s against 387.2 at 342 and 376.7 at 64, 64 x 8 tiles).
 int default_zblock(int nz) {
-    const int blocks = std::max(1, (int)std::lround(nz / 340.0));
+    const int blocks = std::max(1, (int)std::lround(nz / 200.0));
     return (nz + blocks - 1) / blocks;
 }
 

@@ -145,7 +145,7 @@ struct alignas(128) BatchShot {
 // before capturing launches into a graph.
 cudaError_t stream_slots(int tx, int ty, bool batch, int *slots);
 
-// One persistent launch over items[0..nitems) = (shot, item of the shot),
+// One launch over items[0..nitems) = (shot, item of the shot), one CTA each,
 // every shot with the tile tx x ty (stream_tiling_supported).
 cudaError_t launch_step_batch(const BatchShot *shots, const int2 *items, int nitems, int t,
                               const Coeffs &c, unsigned *status, int tx, int ty, cudaStream_t s);
