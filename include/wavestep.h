@@ -56,7 +56,7 @@ extern "C" {
 /* Step kernels selectable with ws_set_kernel. */
 #define WS_KERNEL_AUTO    0  /* the streaming kernel when the grid fits its tile, else DIRECT */
 #define WS_KERNEL_DIRECT  1  /* one thread per cell, neighbours loaded from global memory */
-#define WS_KERNEL_STREAM  2  /* z-streaming: TMA rings + 9-plane register queue, persistent */
+#define WS_KERNEL_STREAM  2  /* z-streaming: TMA rings + 9-plane register queue, one CTA per item */
 
 /* Storage of the two wavefield levels (ws_set_storage). */
 #define WS_STORAGE_FP32   0  /* float32 fields and model: 16 bytes per cell update */
@@ -259,7 +259,7 @@ int ws_autotune(ws_t ws, int *tile_x, int *tile_y, int *zblock);
 /* ---- batched shots -------------------------------------------------------
  * A batch advances several independent handles ("shots": each its own grid
  * size, model, taper, sources and receivers) together: every step is ONE
- * persistent launch of the streaming kernel over the work items of all
+ * launch of the streaming kernel over the work items (one CTA each) of all
  * shots, and each ws_batch_step(n) replays a CUDA graph of n such launches.
  * The results are bit for bit those of ws_step on each handle (the same
  * arithmetic per cell, whatever the tiling). The paper's many-problem use is

@@ -136,7 +136,7 @@ struct ws_handle {
     int stall_item = -1;       // test hook (ws_test_stall), consumed by the next FP32 step
 };
 
-// A group of handles advanced together: one persistent launch per step
+// A group of handles advanced together: one launch per step
 // covers every shot's items; runs of steps are replayed as CUDA graphs.
 struct ws_batch {
     std::vector<ws_t> shots;

@@ -1,7 +1,8 @@
 // Streaming step kernel with 16-bit field storage (BF16 or FP16), velocity form.
 //
-// Same pipeline as the FP32 streaming kernel (persistent CTAs, one TMA
-// producer lane, 9-plane register queue, fused taper/source/receivers), but
+// Same pipeline as the FP32 streaming kernel (one CTA per work item in item
+// order, one TMA producer lane, 9-plane register queue, fused
+// taper/source/receivers), but
 // the state is stored as
 //     U = u^n   and   D = u^n - u^{n-1}   (16 bits each),
 // and the model as FP16 of (V dt/h)^2 * 2^kW16Exp: 10 bytes per cell update
@@ -562,9 +563,8 @@ cudaError_t launch16(const Maps16 &maps, uint16_t *u_out, uint16_t *d_io, const 
     const int tiles_x = (a.g.nx + TX - 1) / TX;
     const int ntiles = tiles_x * ((a.g.ny + TY - 1) / TY);
     const int nitems = ntiles * ((a.g.nz + zb - 1) / zb);
-    const int grid = min(nitems, sms * ctas_per_sm);
-    kern<<<grid, Cfg::kThreads, Cfg::kSmem, s>>>(maps, u_out, d_io, a, sc, step, src_hint, zb,
-                                                 tiles_x, ntiles, nitems, rec_ptr, rec);
+    kern<<<nitems, Cfg::kThreads, Cfg::kSmem, s>>>(maps, u_out, d_io, a, sc, step, src_hint, zb,
+                                                   tiles_x, ntiles, nitems, rec_ptr, rec);
     return cudaGetLastError();
 }
 
