@@ -146,3 +146,35 @@ def test_storage_needs_a_64_wide_grid():
     with pytest.raises(wsb.WaveStepError) as e:
         wsb.ws_set_storage(hd, wsb.WS_STORAGE_BF16)
     assert e.value.code == wsb.WS_ERR_BADARG
+
+
+def test_full_size_accuracy_against_fp32():
+    """The benchmark's 1024^3 survey, 100 steps: each 16-bit mode against FP32
+    storage (itself within 3e-6 of the FP64 oracle there), on the device,
+    in the launch configuration bench.py times (64 x 8 tile, default z
+    block). Bounds from the measured 8.6e-4 (FP16) and 6.2e-3 (BF16)."""
+    import torch
+    w = synthetic.layered_survey(1024, 1024, 1024, nt=100)
+    bound = {"fp32": 0.0, "fp16": 2e-3, "bf16": 1.2e-2}
+    out = {}
+    for storage, name in [(wsb.WS_STORAGE_FP32, "fp32")] + MODES:
+        hd = wsb.ws_create(w.nx, w.ny, w.nz, w.h, w.dt)
+        wsb.ws_set_storage(hd, storage)
+        wsb.ws_set_velocity(hd, w.vel)
+        wsb.ws_set_sponge(hd, *w.sponge)
+        for s in w.sources:
+            wsb.ws_add_source(hd, *s)
+        wsb.ws_set_receivers(hd, w.receivers, w.nt)
+        wsb.ws_step(hd, w.nt)
+        wsb.ws_synchronize(hd)
+        u = torch.empty((w.nz, w.ny, w.nx), dtype=torch.float32, device="cuda")
+        wsb.ws_read_field(hd, u, None)
+        torch.cuda.synchronize()
+        out[name] = u
+        wsb.ws_destroy(hd)
+    ref = out["fp32"].double()
+    nref = torch.linalg.vector_norm(ref).item()
+    for name in ("fp16", "bf16"):
+        err = torch.linalg.vector_norm(out[name].double() - ref).item() / nref
+        print(f"{name}: 1024^3, 100 steps, relative L2 vs FP32 storage {err:.3e}")
+        assert err <= bound[name], (name, err)
