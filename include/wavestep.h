@@ -267,7 +267,9 @@ int ws_autotune(ws_t ws, int *tile_x, int *tile_y, int *zblock);
  * GPU is this library's addition.
  *
  * The batch references the handles (it does not own them; destroy the batch
- * first). Every shot must have nx >= 32 and ny >= 8. Work runs on a stream
+ * first) and sets each shot's streaming tile to its own; the handles stay
+ * usable on their own between batch steps. Every shot must have nx >= 32
+ * and ny >= 8. Work runs on a stream
  * the batch creates, ordered after each shot's pending work on its own
  * stream, and each shot's later work on its own stream is ordered after it.
  *

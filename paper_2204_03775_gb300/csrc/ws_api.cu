@@ -1333,6 +1333,20 @@ int batch_configure(ws_batch_t b, int tx, int ty, int m) {
 // Descriptors and source samples of the next nsteps steps.
 int batch_upload(ws_batch_t b, int nsteps) {
     const int n = (int)b->shots.size();
+    // a shot may have been used on its own since the table was built: its
+    // tensor-map boxes and receiver table must match the batch's tile (a
+    // box larger than the kernel's ring slot would overrun shared memory)
+    for (int q = 0; q < n; ++q) {
+        ws_t ws = b->shots[q];
+        if (ws->tiling.tx != b->tx || ws->tiling.ty != b->ty) {
+            ws->tiling.tx = b->tx;
+            ws->tiling.ty = b->ty;
+            int rc = encode_maps(ws);
+            if (rc != WS_OK) return rc;
+        }
+        int rc = build_rec_tiles(ws, ws::StreamTiling{b->tx, b->ty, b->zb[q]});
+        if (rc != WS_OK) return rc;
+    }
     size_t total = 0;
     for (ws_t ws : b->shots) total += ws->src.size() * size_t(nsteps);
     if (total > b->src_cap) {

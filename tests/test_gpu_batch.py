@@ -171,3 +171,28 @@ def test_full_size_batch_equals_single_shots():
         np.testing.assert_array_equal(wsb.ws_read_traces(h), got_tr[q])
         if q in got_u:
             np.testing.assert_array_equal(wsb.ws_read_field(h)[0], got_u[q])
+
+
+def test_shots_used_alone_between_batch_steps():
+    """A shot stepped on its own with another tile and with new receivers
+    between batch steps: the batch re-encodes its maps and receiver table."""
+    nt = 30
+    shots = [_shot(sh, 60 + q, nt) for q, sh in enumerate(SHAPES[:3])]
+    ref = []
+    for s in shots:
+        hd = _handle(s)
+        wsb.ws_step(hd, nt)
+        ref.append(_state(hd))
+    hs = [_handle(s) for s in shots]
+    b = wsb.ws_batch_create(hs)
+    wsb.ws_batch_set_tiling(b, 64, 8, 2)
+    wsb.ws_batch_step(b, 10)
+    wsb.ws_set_kernel(hs[0], wsb.WS_KERNEL_STREAM, 32, 16, 0)   # another tile
+    wsb.ws_step(hs[0], 5)
+    wsb.ws_batch_step(b, 5)        # hs[0] at 20 steps, the others at 15
+    wsb.ws_step(hs[1], 5)
+    wsb.ws_step(hs[2], 5)
+    wsb.ws_batch_step(b, 10)       # every shot at nt = 30
+    wsb.ws_batch_synchronize(b)
+    for hd, r in zip(hs, ref):     # tiles never change the bits
+        _check_equal(_state(hd), r)
