@@ -142,6 +142,7 @@ class Handle:
         self.shape = shape  # (nz, ny, nx)
         self.nrec = 0
         self.nt_max = 0
+        self.batches = 0    # live batches that reference this handle
 
     def __del__(self):
         if self.ptr and _lib is not None:
@@ -157,6 +158,9 @@ def ws_create(nx: int, ny: int, nz: int, h: float, dt: float) -> Handle:
 
 
 def ws_destroy(ws: Handle) -> None:
+    if ws.batches:
+        raise WaveStepError(WS_ERR_STATE, "ws_destroy: a live batch still references this "
+                                          "handle; destroy the batch first")
     if ws.ptr:
         _check(load_library().ws_destroy(ws.ptr), "ws_destroy")
         ws.ptr = ctypes.c_void_p(None)
@@ -313,11 +317,19 @@ class Batch:
     def __init__(self, ptr: int, shots):
         self.ptr = ctypes.c_void_p(ptr)
         self.shots = list(shots)
+        for h in self.shots:
+            h.batches += 1
 
-    def __del__(self):
+    def _release(self):
         if self.ptr and _lib is not None:
             _lib.ws_batch_destroy(self.ptr)
-            self.ptr = ctypes.c_void_p(None)
+        if self.ptr:
+            for h in self.shots:
+                h.batches -= 1
+        self.ptr = ctypes.c_void_p(None)
+
+    def __del__(self):
+        self._release()
 
 
 def ws_batch_create(shots) -> Batch:
@@ -330,9 +342,7 @@ def ws_batch_create(shots) -> Batch:
 
 
 def ws_batch_destroy(b: Batch) -> None:
-    if b.ptr:
-        _check(load_library().ws_batch_destroy(b.ptr), "ws_batch_destroy")
-        b.ptr = ctypes.c_void_p(None)
+    b._release()
 
 
 def ws_batch_set_tiling(b: Batch, tile_x: int, tile_y: int, zmul: int = 0) -> None:

@@ -546,20 +546,28 @@ __global__ void __launch_bounds__(StreamCfg<TX, TY, NA, NB>::kThreads, MINB)
     stream_body<TX, TY, NA, NB>(src, c, status);
 }
 
-// Resident CTAs per SM and SM count of a kernel (queried once per kernel).
+// Resident CTAs per SM and SM count of a kernel on the current device,
+// looked up (and the kernel's shared-memory limit set) the first time the
+// kernel runs on each device.
 template <class KernFn>
-cudaError_t occupancy(KernFn kern, int threads, size_t smem, int *ctas_per_sm, int *sms) {
-    if (*ctas_per_sm != 0) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+cudaError_t occupancy(KernFn kern, int threads, size_t smem, LaunchFacts &lf, int *ctas_per_sm,
+                      int *sms) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    int dev = 0, n = 0, c = 0;
-    e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, kern, threads, smem);
-    if (e != cudaSuccess) return e;
-    if (c < 1) return cudaErrorInvalidConfiguration;
-    *sms = n;
-    *ctas_per_sm = c;
+    if (dev < 0 || dev >= LaunchFacts::kMaxDevices) return cudaErrorInvalidDevice;
+    if (lf.ctas[dev] == 0) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        int n = 0, c = 0;
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, kern, threads, smem);
+        if (e != cudaSuccess) return e;
+        if (c < 1) return cudaErrorInvalidConfiguration;
+        lf.sms[dev] = n;
+        lf.ctas[dev] = c;
+    }
+    *ctas_per_sm = lf.ctas[dev];
+    *sms = lf.sms[dev];
     return cudaSuccess;
 }
 
@@ -568,8 +576,9 @@ cudaError_t launch_tile_as(const StreamMaps &maps, float *up, const StepArgs &a,
                            const int *rec_ptr, const RecEntry *rec, cudaStream_t s) {
     using Cfg = StreamCfg<TX, TY, NA, NB>;
     auto kern = step_stream_kernel<TX, TY, NA, NB, MINB, kLap>;
-    static int ctas_per_sm = 0, sms = 0;
-    cudaError_t e = occupancy(kern, Cfg::kThreads, Cfg::kSmem, &ctas_per_sm, &sms);
+    static LaunchFacts lf;
+    int ctas_per_sm = 0, sms = 0;
+    cudaError_t e = occupancy(kern, Cfg::kThreads, Cfg::kSmem, lf, &ctas_per_sm, &sms);
     if (e != cudaSuccess) return e;
     const int tiles_x = (a.g.nx + TX - 1) / TX;
     const int ntiles = tiles_x * ((a.g.ny + TY - 1) / TY);
@@ -590,12 +599,13 @@ cudaError_t launch_tile(const StreamMaps &maps, float *up, const StepArgs &a, in
 template <int TX, int TY, int NA, int NB, int MINB>
 cudaError_t slots_of(bool batch, int *slots) {
     using Cfg = StreamCfg<TX, TY, NA, NB>;
-    static int c1 = 0, n1 = 0, c2 = 0, n2 = 0;
+    static LaunchFacts lf_grid, lf_batch;
+    int c = 0, n = 0;
     cudaError_t e = batch ? occupancy(step_batch_kernel<TX, TY, NA, NB, MINB>, Cfg::kThreads,
-                                      Cfg::kSmem, &c2, &n2)
+                                      Cfg::kSmem, lf_batch, &c, &n)
                           : occupancy(step_stream_kernel<TX, TY, NA, NB, MINB, false>,
-                                      Cfg::kThreads, Cfg::kSmem, &c1, &n1);
-    if (e == cudaSuccess) *slots = batch ? c2 * n2 : c1 * n1;
+                                      Cfg::kThreads, Cfg::kSmem, lf_grid, &c, &n);
+    if (e == cudaSuccess) *slots = c * n;
     return e;
 }
 
@@ -604,8 +614,9 @@ cudaError_t launch_batch_tile(const BatchShot *shots, const int2 *items, int nit
                               const Coeffs &c, unsigned *status, cudaStream_t s) {
     using Cfg = StreamCfg<TX, TY, NA, NB>;
     auto kern = step_batch_kernel<TX, TY, NA, NB, MINB>;
-    static int ctas_per_sm = 0, sms = 0;
-    cudaError_t e = occupancy(kern, Cfg::kThreads, Cfg::kSmem, &ctas_per_sm, &sms);
+    static LaunchFacts lf;
+    int ctas_per_sm = 0, sms = 0;
+    cudaError_t e = occupancy(kern, Cfg::kThreads, Cfg::kSmem, lf, &ctas_per_sm, &sms);
     if (e != cudaSuccess) return e;
     kern<<<nitems, Cfg::kThreads, Cfg::kSmem, s>>>(shots, items, nitems, t, c, status);
     return cudaGetLastError();

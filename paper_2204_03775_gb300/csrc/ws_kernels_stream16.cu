@@ -546,19 +546,21 @@ cudaError_t launch16(const Maps16 &maps, uint16_t *u_out, uint16_t *d_io, const 
                      const RecEntry *rec, cudaStream_t s) {
     using Cfg = Cfg16<TX, TY, NA, NB>;
     auto kern = step_stream16_kernel<Fmt, TX, TY, NA, NB, MINB>;
-    static int ctas_per_sm = 0, sms = 0;
-    if (ctas_per_sm == 0) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)Cfg::kSmem);
-        if (e != cudaSuccess) return e;
-        int dev = 0;
-        e = cudaGetDevice(&dev);
-        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    // the shared-memory limit is a per-device property of the kernel
+    static LaunchFacts lf;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= LaunchFacts::kMaxDevices) return cudaErrorInvalidDevice;
+    if (lf.ctas[dev] == 0) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)Cfg::kSmem);
+        int c = 0;
         if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas_per_sm, kern, Cfg::kThreads,
-                                                              Cfg::kSmem);
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, kern, Cfg::kThreads, Cfg::kSmem);
         if (e != cudaSuccess) return e;
-        if (ctas_per_sm < 1) return cudaErrorInvalidConfiguration;
+        if (c < 1) return cudaErrorInvalidConfiguration;
+        lf.ctas[dev] = c;
     }
     const int tiles_x = (a.g.nx + TX - 1) / TX;
     const int ntiles = tiles_x * ((a.g.ny + TY - 1) / TY);

@@ -8,6 +8,13 @@
 
 namespace ws {
 
+// Per-device launch facts of one kernel (see occupancy()).
+struct LaunchFacts {
+    static constexpr int kMaxDevices = 64;
+    int ctas[kMaxDevices] = {};
+    int sms[kMaxDevices] = {};
+};
+
 static __device__ __forceinline__ unsigned smem_addr(const void *p) {
     return static_cast<unsigned>(__cvta_generic_to_shared(p));
 }

@@ -196,3 +196,13 @@ def test_shots_used_alone_between_batch_steps():
     wsb.ws_batch_synchronize(b)
     for hd, r in zip(hs, ref):     # tiles never change the bits
         _check_equal(_state(hd), r)
+
+
+def test_binding_keeps_batched_handles_alive():
+    s = _shot((72, 40, 30), 2, 10)
+    h = _handle(s)
+    b = wsb.ws_batch_create([h])
+    with pytest.raises(wsb.WaveStepError):
+        wsb.ws_destroy(h)                 # the batch still uses it
+    wsb.ws_batch_destroy(b)
+    wsb.ws_destroy(h)
