@@ -212,6 +212,11 @@ int ws_energy_noalloc(const float *u, const float *u_prev, const float *v, int n
  * sums Lap' u^n of their segment (the float values the step used) for the
  * imaging: two forward passes and one backward pass in all.
  *
+ * A residual for the run that the last ws_forward left (WS_ADJ_RESIDUAL,
+ * with no change to the model, taper, sources, receivers or storage since)
+ * reuses that run's checkpoints instead of running the forward problem
+ * again; the handle's state is then left as it is.
+ *
  * Needs a velocity model, receivers and FP32 storage, else STATE. Device
  * scratch: about 3 sqrt(N) + 6 padded fields and two
  * trace arrays, allocated by the first call and kept by the handle for the
@@ -222,6 +227,15 @@ int ws_energy_noalloc(const float *u, const float *u_prev, const float *v, int n
  * TIMEOUT. */
 int ws_adjoint_gradient(ws_t ws, const float *data, int mode, float *grad_m, double *misfit,
                         int on_device);
+
+/* The forward run of ws_adjoint_gradient on its own: fields zeroed, step 0,
+ * nt_max steps with the handle's sources, traces recorded (ws_read_traces),
+ * and the sqrt(N) checkpoint pairs kept in the handle's adjoint scratch, so
+ * that a following ws_adjoint_gradient(WS_ADJ_RESIDUAL) for these traces
+ * skips its own forward run (the torch bridge's forward and backward). The
+ * paper has no counterpart (forward problem only). Same requirements and
+ * scratch as ws_adjoint_gradient; synchronizes nothing. */
+int ws_forward(ws_t ws);
 
 /* Store the state in 16 bits (WS_STORAGE_BF16 or WS_STORAGE_FP16) or back
  * in FP32. The 16-bit modes keep U = u^n and D = u^n - u^{n-1} (the

@@ -13,7 +13,7 @@ from .binding import (  # noqa: F401
     WS_STORAGE_FP16, WS_STORAGE_FP32, Batch, Handle,
     WaveStepError, load_library, ws_add_source, ws_adjoint_gradient, ws_autotune,
     ws_batch_create, ws_batch_destroy, ws_batch_get_tiling, ws_batch_launch_count,
-    ws_batch_set_tiling, ws_batch_step, ws_batch_synchronize, ws_clear_sources, ws_create, ws_destroy, ws_energy,
+    ws_batch_set_tiling, ws_batch_step, ws_batch_synchronize, ws_clear_sources, ws_create, ws_destroy, ws_energy, ws_forward,
     ws_energy_noalloc,
     ws_get_step, ws_last_error, ws_launch_count, ws_read_field, ws_read_traces, ws_set_kernel,
     ws_set_receivers, ws_set_slowness2, ws_set_sponge, ws_set_storage, ws_set_stream, ws_set_velocity, ws_step,

@@ -32,19 +32,23 @@ class Shot:
         b.ws_set_receivers(self.ws, self.receivers, self.nt)
 
     def _bind(self, m: torch.Tensor) -> None:
+        """Give the handle the model m, unless it already holds this very tensor
+        unmodified (then the checkpoints of its last forward run stay usable)."""
         if not (m.is_cuda and m.dtype == torch.float32 and tuple(m.shape) == self.shape):
             raise TypeError(f"m: a float32 CUDA tensor of shape {self.shape}")
         b.ws_set_stream(self.ws, torch.cuda.current_stream(m.device))
-        b.ws_set_slowness2(self.ws, m.contiguous())
+        # the reference to the bound tensor keeps its memory from being reused
+        # by another tensor that would then look identical
+        if getattr(self, "_bound", None) is not m or self._bound_version != m._version:
+            b.ws_set_slowness2(self.ws, m.contiguous())
+            self._bound, self._bound_version = m, m._version
 
 
 class _Traces(torch.autograd.Function):
     @staticmethod
     def forward(ctx, m: torch.Tensor, shot: Shot) -> torch.Tensor:
         shot._bind(m)
-        b.ws_write_field(shot.ws, None, None, 0)
-        b.ws_set_receivers(shot.ws, shot.receivers, shot.nt)
-        b.ws_step(shot.ws, shot.nt)
+        b.ws_forward(shot.ws)          # traces + the checkpoints the backward reuses
         out = torch.empty((len(shot.receivers), shot.nt), dtype=torch.float32, device=m.device)
         b.ws_read_traces(shot.ws, out)
         ctx.save_for_backward(m)

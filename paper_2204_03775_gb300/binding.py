@@ -71,6 +71,7 @@ def load_library(build_if_missing: bool = False):
         "ws_set_velocity": (i, [vp, vp, i]),
         "ws_set_slowness2": (i, [vp, vp, i]),
         "ws_adjoint_gradient": (i, [vp, vp, i, vp, ctypes.POINTER(d), i]),
+        "ws_forward": (i, [vp]),
         "ws_set_sponge": (i, [vp, i, d]),
         "ws_add_source": (i, [vp, i, i, i, d, d, d]),
         "ws_clear_sources": (i, [vp]),
@@ -202,6 +203,11 @@ def ws_adjoint_gradient(ws: Handle, data, mode: int = WS_ADJ_DATA, grad_m=None):
                                               ctypes.c_void_p(pg), ctypes.byref(j), dd),
            "ws_adjoint_gradient")
     return grad_m, j.value
+
+
+def ws_forward(ws: Handle) -> None:
+    """Forward run from rest over nt_max steps, keeping the adjoint's checkpoints."""
+    _check(load_library().ws_forward(ws.ptr), "ws_forward")
 
 
 def ws_set_sponge(ws: Handle, nb: int, a: float) -> None:

@@ -133,6 +133,9 @@ struct ws_handle {
 
     // device scratch of ws_adjoint_gradient, kept for the next call
     struct AdjointCache *adj = nullptr;
+    // bumped by every call that changes what a forward run from rest computes
+    // (model, taper, sources, receivers, storage)
+    unsigned long long model_version = 0;
     int stall_item = -1;       // test hook (ws_test_stall), consumed by the next FP32 step
 };
 
@@ -175,6 +178,9 @@ struct MappedField {
 // arrays. Reused while the step count, receivers and tiling stay the same.
 struct AdjointCache {
     int N = -1, nrec = -1, kern = -1, tx = 0, ty = 0;
+    // the checkpoints hold the forward run of this model version (ws_forward)
+    bool fwd_valid = false;
+    unsigned long long fwd_version = 0;
     std::vector<void *> mem;        // everything below, for cudaFree
     std::vector<float *> ck;
     std::vector<float *> lap;       // L u^n of the segment's steps
@@ -617,6 +623,7 @@ int ws_set_stream(ws_t ws, void *cuda_stream) {
 
 int ws_set_velocity(ws_t ws, const float *v, int on_device) {
     if (!ws || !v) return fail(WS_ERR_BADARG, "ws_set_velocity: NULL argument");
+    ws->model_version++;
     ws->vel_ok = false;
     int rc = copy_in(ws, ws->w, v, on_device);
     if (rc != WS_OK) return rc;
@@ -646,6 +653,7 @@ int ws_set_velocity(ws_t ws, const float *v, int on_device) {
 
 int ws_set_slowness2(ws_t ws, const float *m, int on_device) {
     if (!ws || !m) return fail(WS_ERR_BADARG, "ws_set_slowness2: NULL argument");
+    ws->model_version++;
     ws->vel_ok = false;
     int rc = copy_in(ws, ws->w, m, on_device);
     if (rc != WS_OK) return rc;
@@ -680,6 +688,7 @@ int ws_set_sponge(ws_t ws, int nb, double a) {
         return fail(WS_ERR_BADARG, "ws_set_sponge: need nb >= 0 and finite a >= 0");
     ws->nb = nb;
     ws->a = a;
+    ws->model_version++;
     return upload_profiles(ws);
 }
 
@@ -693,12 +702,14 @@ int ws_add_source(ws_t ws, int ix, int iy, int iz, double f0, double t0, double 
     if ((int)ws->src.size() >= ws::kMaxSources)
         return fail(WS_ERR_BADARG, "ws_add_source: at most %d sources", ws::kMaxSources);
     ws->src.push_back({ix, iy, iz, f0, t0, amp});
+    ws->model_version++;
     return WS_OK;
 }
 
 int ws_clear_sources(ws_t ws) {
     if (!ws) return fail(WS_ERR_BADARG, "ws_clear_sources: NULL handle");
     ws->src.clear();
+    ws->model_version++;
     return WS_OK;
 }
 
@@ -716,6 +727,7 @@ int ws_set_receivers(ws_t ws, int nrec, const int *ijk, int nt_max) {
     if (nrec > 0 && (long long)nrec * nt_max > (1ll << 40))
         return fail(WS_ERR_BADARG, "ws_set_receivers: trace buffer too large");
     WS_CUDA(cudaStreamSynchronize(ws->stream), "ws_set_receivers");
+    ws->model_version++;
     free_receivers(ws);
     ws->nrec = 0;
     ws->nt_max = 0;
@@ -742,6 +754,7 @@ int ws_set_storage(ws_t ws, int storage) {
     if (storage != WS_STORAGE_FP32 && storage != WS_STORAGE_BF16 && storage != WS_STORAGE_FP16)
         return fail(WS_ERR_BADARG, "ws_set_storage: unknown storage %d", storage);
     if (storage == ws->storage) return WS_OK;
+    ws->model_version++;
     if (storage != WS_STORAGE_FP32 && (ws->g.nx < kTile16X || ws->g.ny < kTile16Y))
         return fail(WS_ERR_BADARG,
                     "ws_set_storage: 16-bit storage needs nx >= %d and ny >= %d (grid %d x %d)",
@@ -961,15 +974,17 @@ int ws_energy_noalloc(const float *u, const float *u_prev, const float *v, int n
     return WS_OK;
 }
 
-int ws_adjoint_gradient(ws_t ws, const float *data, int mode, float *grad_m, double *misfit,
-                        int on_device) {
-    if (!ws || !data || !grad_m) return fail(WS_ERR_BADARG, "ws_adjoint_gradient: NULL argument");
-    if (mode != WS_ADJ_DATA && mode != WS_ADJ_RESIDUAL)
-        return fail(WS_ERR_BADARG, "ws_adjoint_gradient: unknown mode %d", mode);
-    if (!ws->vel_ok) return fail(WS_ERR_STATE, "ws_adjoint_gradient: no valid velocity model");
-    if (ws->nrec == 0) return fail(WS_ERR_STATE, "ws_adjoint_gradient: no receivers");
-    if (ws->storage != WS_STORAGE_FP32)
-        return fail(WS_ERR_STATE, "ws_adjoint_gradient: needs FP32 field storage");
+}  // extern "C"
+
+namespace {
+
+// Checks shared by ws_forward and ws_adjoint_gradient; selects the kernel and
+// makes sure the handle's adjoint scratch matches the run (N = nt_max steps).
+int adjoint_prepare(ws_t ws, const char *who, int *kern_out, ws::StreamTiling *tiling_out,
+                    AdjointCache **acp) {
+    if (!ws->vel_ok) return fail(WS_ERR_STATE, "%s: no valid velocity model", who);
+    if (ws->nrec == 0) return fail(WS_ERR_STATE, "%s: no receivers", who);
+    if (ws->storage != WS_STORAGE_FP32) return fail(WS_ERR_STATE, "%s: needs FP32 field storage", who);
     const ws::Geom &g = ws->g;
     const int N = ws->nt_max;
     const int C = (int)std::ceil(std::sqrt((double)N));    // states per segment
@@ -1048,29 +1063,25 @@ int ws_adjoint_gradient(ws_t ws, const float *data, int mode, float *grad_m, dou
         ac->tx = ws->tiling.tx;
         ac->ty = ws->tiling.ty;
     } else {
-        for (auto &f : ac->rho) WS_CUDA(cudaMemsetAsync(f.p, 0, fb, st), "zero adjoint field");
     }
-    std::vector<float *> &ck = ac->ck;
-    std::vector<float *> &lap = ac->lap;
-    MappedField *ring = ac->ring;
-    MappedField *rho = ac->rho;
-    float2 *acc = ac->acc;
-    double *partials = ac->partials;
-    float *r = ac->r, *grad = on_device ? grad_m : ac->grad;
-    const float *d = data;
-    int *rec = ac->rec;
-    const int np = ws::residual_partial_count();
-    WS_CUDA(cudaMemsetAsync(acc, 0, 2 * fb, st), "zero gradient accumulator");
-    WS_CUDA(cudaMemcpyAsync(rec, ws->rec_ijk.data(), sizeof(int) * 3 * ws->nrec,
-                            cudaMemcpyHostToDevice, st),
-            "upload receivers");
-    if (!on_device) {
-        WS_CUDA(cudaMemcpyAsync(ac->dd, data, sizeof(float) * ntr, cudaMemcpyHostToDevice, st),
-                "upload observed data");
-        d = ac->dd;
-    }
+    *kern_out = kern;
+    *tiling_out = tiling;
+    *acp = ac;
+    return WS_OK;
+}
 
-    // 1. forward from rest, recording the traces and the checkpoints
+// The forward run from rest over N steps: traces recorded, checkpoint pairs
+// (u^{jC}, u^{jC-1}) saved; the cache then holds this model version's run.
+int adjoint_forward(ws_t ws, AdjointCache *ac, int kern, const ws::StreamTiling &tiling) {
+    const ws::Geom &g = ws->g;
+    const int N = ws->nt_max;
+    const int C = (int)std::ceil(std::sqrt((double)N));
+    const size_t fb = field_bytes(g);
+    const size_t ntr = size_t(ws->nrec) * N;
+    const cudaStream_t st = ws->stream;
+    std::vector<float *> &ck = ac->ck;
+    int rc = WS_OK;
+    ac->fwd_valid = false;
     for (int b = 0; b < 2; ++b) WS_CUDA(cudaMemsetAsync(ws->buf[b], 0, fb, st), "zero fields");
     WS_CUDA(cudaMemsetAsync(ws->traces, 0, sizeof(float) * ntr, st), "zero traces");
     ws->step = 0;
@@ -1092,6 +1103,73 @@ int ws_adjoint_gradient(ws_t ws, const float *data, int mode, float *grad_m, dou
         ws->cur = 1 - c;
         ws->step++;
     }
+
+    ac->fwd_valid = true;
+    ac->fwd_version = ws->model_version;
+    return WS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ws_forward(ws_t ws) {
+    if (!ws) return fail(WS_ERR_BADARG, "ws_forward: NULL handle");
+    int kern = WS_KERNEL_STREAM;
+    ws::StreamTiling tiling{};
+    AdjointCache *ac = nullptr;
+    int rc = adjoint_prepare(ws, "ws_forward", &kern, &tiling, &ac);
+    if (rc != WS_OK) return rc;
+    return adjoint_forward(ws, ac, kern, tiling);
+}
+
+int ws_adjoint_gradient(ws_t ws, const float *data, int mode, float *grad_m, double *misfit,
+                        int on_device) {
+    if (!ws || !data || !grad_m) return fail(WS_ERR_BADARG, "ws_adjoint_gradient: NULL argument");
+    if (mode != WS_ADJ_DATA && mode != WS_ADJ_RESIDUAL)
+        return fail(WS_ERR_BADARG, "ws_adjoint_gradient: unknown mode %d", mode);
+    int kern = WS_KERNEL_STREAM;
+    ws::StreamTiling tiling{};
+    AdjointCache *ac = nullptr;
+    int rc = adjoint_prepare(ws, "ws_adjoint_gradient", &kern, &tiling, &ac);
+    if (rc != WS_OK) return rc;
+    const ws::Geom &g = ws->g;
+    const int N = ws->nt_max;
+    const int C = (int)std::ceil(std::sqrt((double)N));    // states per segment
+    const int nck = (N + C - 1) / C;                        // segments
+    const size_t fb = field_bytes(g);
+    const size_t ncell = size_t(g.nx) * g.ny * g.nz;
+    const size_t ntr = size_t(ws->nrec) * N;
+    const cudaStream_t st = ws->stream;
+    for (auto &f : ac->rho) WS_CUDA(cudaMemsetAsync(f.p, 0, fb, st), "zero adjoint field");
+    std::vector<float *> &ck = ac->ck;
+    std::vector<float *> &lap = ac->lap;
+    MappedField *ring = ac->ring;
+    MappedField *rho = ac->rho;
+    float2 *acc = ac->acc;
+    double *partials = ac->partials;
+    float *r = ac->r, *grad = on_device ? grad_m : ac->grad;
+    const float *d = data;
+    int *rec = ac->rec;
+    const int np = ws::residual_partial_count();
+    WS_CUDA(cudaMemsetAsync(acc, 0, 2 * fb, st), "zero gradient accumulator");
+    WS_CUDA(cudaMemcpyAsync(rec, ws->rec_ijk.data(), sizeof(int) * 3 * ws->nrec,
+                            cudaMemcpyHostToDevice, st),
+            "upload receivers");
+    if (!on_device) {
+        WS_CUDA(cudaMemcpyAsync(ac->dd, data, sizeof(float) * ntr, cudaMemcpyHostToDevice, st),
+                "upload observed data");
+        d = ac->dd;
+    }
+
+    // 1. forward from rest, recording the traces and the checkpoints; a
+    // residual given for the run that ws_forward left in the cache (same
+    // model version) needs no new forward run
+    if (!(mode == WS_ADJ_RESIDUAL && ac->fwd_valid && ac->fwd_version == ws->model_version)) {
+        rc = adjoint_forward(ws, ac, kern, tiling);
+        if (rc != WS_OK) return rc;
+    }
+    ws::StepArgs a = base_args(ws);
 
     // 2. residual and misfit
     WS_CUDA(ws::launch_residual(mode == WS_ADJ_DATA ? ws->traces : d,

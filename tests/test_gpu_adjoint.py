@@ -223,3 +223,36 @@ def test_autograd_function_two_shots():
         jsum += j
     np.testing.assert_allclose(m.grad.cpu().numpy(), ref, rtol=1e-6, atol=1e-6 * np.abs(ref).max())
     assert float(loss.detach()) == pytest.approx(jsum, rel=1e-5)
+
+
+def test_forward_then_residual_gradient_reuses_the_run():
+    """ws_forward keeps the checkpoints; a residual-mode gradient right after
+    it skips its own forward run and gives the same bits; any change to the
+    model in between forces a new forward run (and the right gradient)."""
+    nx, ny, nz, nt = 72, 20, 16, 40
+    vel, h, dt, src, rec, sponge, _ = _case(nx, ny, nz, nt, seed=21)
+    r = np.random.default_rng(3).standard_normal((len(rec), nt)).astype(np.float32)
+    hd, g_full, _ = _gpu(vel, h, dt, nt, src, rec, sponge, r, mode=wsb.WS_ADJ_RESIDUAL)
+    h2 = wsb.ws_create(nx, ny, nz, h, dt)
+    wsb.ws_set_velocity(h2, vel)
+    wsb.ws_set_sponge(h2, *sponge)
+    for s in src:
+        wsb.ws_add_source(h2, *s)
+    wsb.ws_set_receivers(h2, rec, nt)
+    wsb.ws_forward(h2)
+    np.testing.assert_array_equal(wsb.ws_read_traces(h2), wsb.ws_read_traces(hd))
+    launches = wsb.ws_launch_count(h2)
+    g_reuse, _ = wsb.ws_adjoint_gradient(h2, r, wsb.WS_ADJ_RESIDUAL)
+    used = wsb.ws_launch_count(h2) - launches
+    np.testing.assert_array_equal(g_reuse, g_full)
+    launches = wsb.ws_launch_count(h2)
+    wsb.ws_adjoint_gradient(h2, r, wsb.WS_ADJ_RESIDUAL)          # still the same run: reused
+    assert wsb.ws_launch_count(h2) - launches == used
+    # a new model: the forward run is redone, so more launches, other values
+    wsb.ws_set_velocity(h2, (vel * 1.01).astype(np.float32))
+    launches = wsb.ws_launch_count(h2)
+    g_new, _ = wsb.ws_adjoint_gradient(h2, r, wsb.WS_ADJ_RESIDUAL)
+    assert wsb.ws_launch_count(h2) - launches >= used + nt
+    _, g_ref, _ = _gpu((vel * 1.01).astype(np.float32), h, dt, nt, src, rec, sponge, r,
+                       mode=wsb.WS_ADJ_RESIDUAL)
+    np.testing.assert_array_equal(g_new, g_ref)
