@@ -263,7 +263,8 @@ int ws_set_kernel(ws_t ws, int kernel, int tile_x, int tile_y, int zblock);
 
 /* Pick the streaming kernel's tile and z-block for this handle's grid by
  * timing the candidates (every tile that fits; z-blocks giving the default
- * length and about 1, 2, 4 and 8 x the resident CTAs in work items) on
+ * length and item counts just below and just above 1 .. 8 waves of the
+ * resident CTAs) on
  * steps written to a scratch field, so the state is unchanged; then select
  * WS_KERNEL_STREAM with the fastest (WS_KERNEL_DIRECT if no tile fits).
  * Results are cached per grid size for the process. Outputs may be NULL.

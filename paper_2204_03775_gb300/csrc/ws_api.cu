@@ -243,15 +243,15 @@ int default_zblock(int nz) {
     return (nz + blocks - 1) / blocks;
 }
 
-// The default, shortened on small grids until there are at least two items
-// per resident CTA (a 256^3 grid in 64 x 8 tiles has 128 tiles for 456
-// CTAs: one 256-plane block per tile ran at 139 Gcell/s, 32-plane blocks at
-// more than twice that).
+// The default, shortened on small grids to about two full waves of items
+// over the resident CTAs (a 256^3 grid in 64 x 8 tiles has 128 tiles for 456
+// CTAs: one 256-plane block per tile ran at 139 Gcell/s, short blocks at
+// more than twice that); the count is rounded down so the last wave is full.
 int default_zblock(const ws::Geom &g, int tx, int ty) {
     int zb = default_zblock(g.nz), slots = 0;
     if (ws::stream_slots(tx, ty, false, &slots) != cudaSuccess) return zb;
     const long long tiles = (long long)((g.nx + tx - 1) / tx) * ((g.ny + ty - 1) / ty);
-    const long long blocks = std::max<long long>(1, (2LL * slots + tiles - 1) / tiles);
+    const long long blocks = std::max<long long>(1, 2LL * slots / tiles);
     const int zs = (int)std::max<long long>(8, (g.nz + blocks - 1) / blocks);
     return std::min(zb, std::min(zs, g.nz));
 }
@@ -513,15 +513,18 @@ void destroy(ws_t ws) {
 constexpr int kTileCands[5][2] = {{64, 8}, {32, 8}, {32, 16}, {64, 16}, {64, 32}};
 
 // z-block candidates for a grid of nz planes cut into `tiles` xy tiles: the
-// default, and blocks that give about m x slots items (m = 1, 2, 4, 8), i.e.
-// enough items to fill every resident CTA several times over on small grids.
+// default, and for m = 1 .. 8 the z blocks whose item count comes closest to
+// m waves of the resident CTAs from below and from above (a wave that is only
+// partly filled leaves SMs idle at the end of every step on small grids).
 std::vector<int> zblock_candidates(int nz, long long tiles, int slots) {
     std::vector<int> z{default_zblock(nz)};
-    for (int m : {1, 2, 4, 8}) {
+    for (int m = 1; m <= 8; ++m) {
         const long long target = (long long)m * slots;
-        const long long blocks = std::max<long long>(1, (target + tiles - 1) / tiles);
-        const int zb = (int)std::max<long long>(8, (nz + blocks - 1) / blocks);
-        z.push_back(std::min(zb, nz));
+        for (long long blocks : {target / tiles, (target + tiles - 1) / tiles}) {
+            blocks = std::max<long long>(1, blocks);
+            const int zb = (int)std::max<long long>(8, (nz + blocks - 1) / blocks);
+            z.push_back(std::min(zb, nz));
+        }
     }
     std::sort(z.begin(), z.end());
     z.erase(std::unique(z.begin(), z.end()), z.end());
@@ -1373,10 +1376,10 @@ int batch_configure(ws_batch_t b, int tx, int ty, int m) {
         const ws::Geom &g = ws->g;
         const long long tiles = (long long)((g.nx + tx - 1) / tx) * ((g.ny + ty - 1) / ty);
         int zb = default_zblock(g.nz);
-        if (m > 0) {
+        if (m > 0) {   // this shot's share of m waves, rounded down to whole blocks
             const double share = double(g.nx) * g.ny * g.nz / double(cells);
             const long long want = std::max<long long>(1, std::llround(m * slots * share));
-            const long long blocks = std::max<long long>(1, (want + tiles - 1) / tiles);
+            const long long blocks = std::max<long long>(1, want / tiles);
             zb = (int)std::min<long long>(g.nz, std::max<long long>(8, (g.nz + blocks - 1) / blocks));
         }
         b->zb[q] = zb;
@@ -1553,7 +1556,7 @@ int ws_batch_create(ws_batch_t *out, int nshots, const ws_t *shots) {
         bool fits = true;
         for (ws_t ws : b->shots) fits = fits && ws->g.nx >= tc[0] && ws->g.ny >= tc[1];
         if (!fits) continue;
-        for (int m : {0, 1, 2, 4, 8}) b->todo.push_back(ws_batch::Cand{tc[0], tc[1], m});
+        for (int m : {0, 1, 2, 3, 4, 6}) b->todo.push_back(ws_batch::Cand{tc[0], tc[1], m});
     }
     if (b->todo.empty()) {
         batch_free(b);
