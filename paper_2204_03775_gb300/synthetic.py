@@ -22,11 +22,12 @@ hundreds to a thousand cells per axis, 1000 steps, Section IV):
   benchmark's workload, smaller sizes are parity cases.
 * ``adjoint_survey`` -- gradient workload: the layered model as the start
   (background) model, the true model the background times
-  1 + 0.1 exp(-|x - c|^2 / (2 s^2)) (a +10% Gaussian blob, s = n/12, centre c
-  drawn from the seed inside the middle half of the grid), a 4 x 4 grid of
-  10 Hz Ricker shots and a 128 x 128 receiver grid on the plane k = 20,
-  a 20-cell absorbing layer, dt at CFL 0.4 of the faster (true) model;
-  256^3 with 800 steps is the full size.
+  1 + 0.1 exp(-|x - c|^2 / (2 s^2)) (a +10% Gaussian blob, s = 12 cells,
+  centre c drawn from the seed: 20 to 40 cells below the plane k = 20 and
+  laterally inside the middle half), a 4 x 4 grid of 10 Hz Ricker shots and
+  a 128 x 128 receiver grid on the plane k = 20, a 20-cell absorbing layer,
+  dt at CFL 0.4 of the faster (true) model; 256^3 with 800 steps is the
+  full size.
 * ``batched_shots`` -- 64 independent shots on grids whose sizes are drawn
   from the seed (nx, ny uniform in [96, 320], nz in [96, 256]), each with
   its own smooth random model in [1500, 4500] m/s (``smooth_random_velocity``,
@@ -156,13 +157,16 @@ def adjoint_survey(n: int = 256, nt: int = 800, shots_side: int = 4, rec_side: i
                    seed: int = 2204) -> AdjointSurvey:
     bg = layered_model(n, n, n, seed=seed)
     rng = np.random.Generator(np.random.PCG64(seed + 1))
-    c = rng.uniform(n / 4, 3 * n / 4, 3)              # blob centre (k, j, i)
-    s = n / 12.0
+    # blob centre (k, j, i): laterally in the middle half, 20 to 40 cells below
+    # the shot/receiver plane, so its reflections reach the receivers within
+    # the 800 steps (deeper, they would arrive after the recording ends)
+    plane = min(nb, n - 1)
+    c = np.array([rng.uniform(plane + 20, plane + 40), *rng.uniform(n / 4, 3 * n / 4, 2)])
+    s = 12.0
     k, j, i = np.ogrid[:n, :n, :n]
     r2 = (k - c[0]) ** 2 + (j - c[1]) ** 2 + (i - c[2]) ** 2
     true = (bg * (1.0 + 0.1 * np.exp(-r2 / (2.0 * s * s)))).astype(np.float32)
     dt = cfl_dt(float(true.max()), h)
-    plane = min(nb, n - 1)
     margin = min(nb, n // 4)
     side = min(rec_side, n - 2 * margin)
     rec = surface_receivers(n, n, plane, side, margin)
