@@ -401,6 +401,25 @@ def adjoint_report():
         times.append(time.perf_counter() - t0)
     for h in hs:
         wsb.ws_destroy(h)
+    del hs
+
+    # the same 16-shot misfit and gradient through the torch bridge (the call a
+    # user makes): traces(m) per shot, loss, backward; the backward reuses
+    # each shot's forward run
+    from paper_2204_03775_gb300 import autograd as wsa
+    shots = [wsa.Shot((w.nz, w.ny, w.nx), w.h, w.dt, w.nt, shot, w.receivers, w.sponge)
+             for shot in w.shots]
+    auto_times = []
+    for rep in range(2):
+        m = m0.clone().requires_grad_(True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        loss = sum(0.5 * ((wsa.traces(m, sh) - d) ** 2).sum() for sh, d in zip(shots, d_obs))
+        loss.backward()
+        torch.cuda.synchronize()
+        auto_times.append(time.perf_counter() - t0)
+    auto_rel = float((m.grad - g).abs().max() / g.abs().max())
+    del shots
     cells = w.nx * w.ny * w.nz
     return {"workload": f"adjoint_survey {w.nx}^3, 16 shots, {nrec} receivers, {w.nt} steps, "
                         "true = layered + 10% Gaussian blob, start = layered",
@@ -411,6 +430,10 @@ def adjoint_report():
             "tiling": {"tile": f"{tiling[0]}x{tiling[1]}", "zblock": tiling[2]},
             "passes": "forward (traces + sqrt(N) checkpoints), residual, then per segment a "
                       "recomputation and the adjoint steps with injection and imaging",
+            "torch_autograd": {"forward_backward_s": min(auto_times),
+                               "grad_vs_ws_adjoint_gradient": auto_rel,
+                               "what": "loss = sum over shots of 0.5 |traces(m) - d|^2; "
+                                       "loss.backward() (ws_forward + residual-mode adjoint)"},
             "timing": "host clock, 16 shots one after another"}
 
 

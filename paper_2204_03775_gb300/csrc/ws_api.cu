@@ -1,21 +1,8 @@
-// Host side of the C ABI declared in include/wavestep.h.
-#include <cudaTypedefs.h>
+// Host side of the C ABI declared in include/wavestep.h: the handle, its
+// buffers and tensor maps, and the entry points of the forward stepper.
+#include "ws_host.h"
 
-#include <algorithm>
-#include <cmath>
-#include <cstdarg>
-#include <cstdio>
-#include <cstring>
-#include <map>
-#include <mutex>
-#include <new>
-#include <tuple>
-#include <type_traits>
-#include <vector>
-
-#include "ws_internal.h"
-
-namespace {
+namespace wsh {
 
 thread_local char g_err[512] = "";
 
@@ -32,16 +19,6 @@ int cuda_fail(cudaError_t e, const char *what) {
         return fail(WS_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
     return fail(WS_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
-
-#define WS_CUDA(call, what)                              \
-    do {                                                 \
-        cudaError_t e_ = (call);                         \
-        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
-    } while (0)
-
-// The 1D weights of the 8th-order second difference, offsets 0..4.
-constexpr double kW0 = -205.0 / 72.0, kW1 = 8.0 / 5.0, kW2 = -1.0 / 5.0, kW3 = 8.0 / 315.0,
-                 kW4 = -1.0 / 560.0;
 
 // Leapfrog stability limit of V dt / h for the 3D 25-point Laplacian: the
 // largest |eigenvalue| times h^2 is 3 (|w0| + 2 sum |wm|) (the checkerboard
@@ -67,11 +44,6 @@ double taper(int idx, int n, int nb, double a) {
     return std::exp(-x * x);
 }
 
-struct SourceDef {
-    int i, j, k;
-    double f0, t0, amp;
-};
-
 PFN_cuTensorMapEncodeTiled_v12000 get_encode_fn() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     if (fn) return fn;
@@ -85,123 +57,12 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode_fn() {
     return fn;
 }
 
-}  // namespace
-
-struct ws_handle {
-    ws::Geom g{};
-    double h = 0, dt = 0;
-    float *buf[2] = {nullptr, nullptr};  // the two wavefield levels
-    int cur = 0;                         // buf[cur] = u^n, buf[1-cur] = u^{n-1}
-    float *w = nullptr;                  // (V dt / h)^2, padded
-    float *gx = nullptr, *gy = nullptr, *gz = nullptr;
-    unsigned *status = nullptr;          // [0] status bits, [1] vmax bits, [2] vmin bits
-    double *energy = nullptr;            // energy partial sums, then the total
-    cudaStream_t stream = nullptr;
-    bool vel_ok = false;
-    int nb = 0;
-    double a = 0;
-    long long step = 0;
-    std::vector<SourceDef> src;
-
-    int nrec = 0, nt_max = 0;
-    long long trace_start = 0;
-    std::vector<int> rec_ijk;
-    float *traces = nullptr;
-    long long *rec_pidx = nullptr;       // direct path
-    int *rec_ptr = nullptr;              // streaming path: per-tile ranges
-    ws::RecEntry *rec_entries = nullptr;
-    int rec_tiling_tx = 0, rec_tiling_ty = 0;
-
-    int kernel = WS_KERNEL_AUTO;
-    ws::StreamTiling tiling{64, 8, 0};
-    CUtensorMap tmap_halo[2];  // buf[b] with the (tx+8, ty+8, 1) box
-    CUtensorMap tmap_tile[2];  // buf[b] with the (tx, ty, 1) box
-    CUtensorMap tmap_w;        // w with the (tx, ty, 1) box
-    bool tmap_ok = false;
-    long long launches = 0;
-
-    // 16-bit storage (WS_STORAGE_BF16 / WS_STORAGE_FP16): the state lives in
-    // buf16[cur] (u^n) and d16 (u^n - u^{n-1}), the model in w16 as well as
-    // w; buf then serves as FP32 scratch copies.
-    int storage = WS_STORAGE_FP32;
-    uint16_t *buf16[2] = {nullptr, nullptr};
-    uint16_t *d16 = nullptr, *w16 = nullptr;
-    bool w16_ok = false;       // w16 holds the current model
-    ws::Scale16 *scale = nullptr;
-    CUtensorMap t16_halo[2], t16_d, t16_w;
-    double wmax = 0.0;         // max (V dt / h)^2 of the model
-
-    // device scratch of ws_adjoint_gradient, kept for the next call
-    struct AdjointCache *adj = nullptr;
-    // bumped by every call that changes what a forward run from rest computes
-    // (model, taper, sources, receivers, storage)
-    unsigned long long model_version = 0;
-    int stall_item = -1;       // test hook (ws_test_stall), consumed by the next FP32 step
-};
-
-// A group of handles advanced together: one launch per step
-// covers every shot's items; runs of steps are replayed as CUDA graphs.
-struct ws_batch {
-    std::vector<ws_t> shots;
-    cudaStream_t stream = nullptr;     // the batch's own stream (graphs need one)
-    cudaEvent_t ev = nullptr;
-    cudaEvent_t t0 = nullptr, t1 = nullptr, t2 = nullptr;
-    int tx = 0, ty = 0;                // current tile (0: none yet)
-    std::vector<int> zb;               // per shot
-    ws::BatchShot *d_shots = nullptr;
-    int2 *d_items = nullptr;
-    int nitems = 0;
-    ws::SourceSample *d_src = nullptr;
-    size_t src_cap = 0;
-    unsigned *status = nullptr;
-    std::map<int, cudaGraphExec_t> graphs;   // by number of steps
-    // online tuning: candidates still to time, and the best so far
-    struct Cand {
-        int tx, ty, m;                 // m: target items = m x resident CTAs (0: default z-blocks)
-    };
-    std::vector<Cand> todo;
-    bool tuned = false, fixed = false;
-    Cand best{0, 0, 0};
-    Cand cfg{0, 0, -1};                // what the item table was built for
-    float best_ms = 1e30f;
-    long long launches = 0;
-};
-
-// A padded FP32 field with the streaming kernel's two boxes on it.
-struct MappedField {
-    float *p = nullptr;
-    CUtensorMap halo, tile;
-};
-
-// Scratch of ws_adjoint_gradient: checkpoint pairs, the states of one
-// segment, the two adjoint levels, the gradient accumulator and the trace
-// arrays. Reused while the step count, receivers and tiling stay the same.
-struct AdjointCache {
-    int N = -1, nrec = -1, kern = -1, tx = 0, ty = 0;
-    // the checkpoints hold the forward run of this model version (ws_forward)
-    bool fwd_valid = false;
-    unsigned long long fwd_version = 0;
-    std::vector<void *> mem;        // everything below, for cudaFree
-    std::vector<float *> ck;
-    std::vector<float *> lap;       // L u^n of the segment's steps
-    MappedField ring[2], rho[2];    // recomputed u^n / u^{n-1}; rho^{k+1} / rho^{k+2}
-    float2 *acc = nullptr;          // compensated FP32 gradient sums, padded layout
-    double *partials = nullptr;
-    float *r = nullptr, *dd = nullptr, *grad = nullptr;
-    int *rec = nullptr;
-    ~AdjointCache() {
-        for (void *p : mem) cudaFree(p);
-    }
-};
-
-namespace {
-
 size_t field_bytes(const ws::Geom &g) {
     return size_t(g.pnx) * size_t(g.pny) * size_t(g.pnz) * sizeof(float);
 }
 
 int encode_map(CUtensorMap *map, void *base, const ws::Geom &g, int bx, int by,
-               int elem_bytes = 4) {
+               int elem_bytes) {
     PFN_cuTensorMapEncodeTiled_v12000 enc = get_encode_fn();
     if (!enc) return fail(WS_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
     cuuint64_t dims[3] = {(cuuint64_t)g.pnx, (cuuint64_t)g.pny, (cuuint64_t)g.pnz};
@@ -377,9 +238,6 @@ int upload_profiles(ws_t ws) {
     return WS_OK;
 }
 
-// The tile of the 16-bit streaming kernel.
-constexpr int kTile16X = 64, kTile16Y = 8;
-
 int encode_maps16(ws_t ws) {
     const ws::Geom &g = ws->g;
     int rc = WS_OK;
@@ -508,56 +366,9 @@ void destroy(ws_t ws) {
     delete ws;
 }
 
+}  // namespace wsh
 
-// Tiles of the streaming kernel, in the order the tuners try them.
-constexpr int kTileCands[5][2] = {{64, 8}, {32, 8}, {32, 16}, {64, 16}, {64, 32}};
-
-// z-block candidates for a grid of nz planes cut into `tiles` xy tiles: the
-// default, and for m = 1 .. 8 the z blocks whose item count comes closest to
-// m waves of the resident CTAs from below and from above (a wave that is only
-// partly filled leaves SMs idle at the end of every step on small grids).
-std::vector<int> zblock_candidates(int nz, long long tiles, int slots) {
-    std::vector<int> z{default_zblock(nz)};
-    for (int m = 1; m <= 8; ++m) {
-        const long long target = (long long)m * slots;
-        for (long long blocks : {target / tiles, (target + tiles - 1) / tiles}) {
-            blocks = std::max<long long>(1, blocks);
-            const int zb = (int)std::max<long long>(8, (nz + blocks - 1) / blocks);
-            z.push_back(std::min(zb, nz));
-        }
-    }
-    std::sort(z.begin(), z.end());
-    z.erase(std::unique(z.begin(), z.end()), z.end());
-    return z;
-}
-
-std::mutex g_tune_mutex;
-std::map<std::tuple<int, int, int>, ws::StreamTiling> g_tune_cache;
-
-
-
-// Device scratch of one call: freed, after the stream drains, on every return.
-struct Scratch {
-    cudaStream_t stream;
-    std::vector<void *> ptrs;
-    explicit Scratch(cudaStream_t s) : stream(s) {}
-    ~Scratch() {
-        cudaStreamSynchronize(stream);
-        for (void *p : ptrs) cudaFree(p);
-    }
-    template <class T>
-    cudaError_t alloc(T **p, size_t bytes) {
-        void *q = nullptr;
-        cudaError_t e = cudaMalloc(&q, bytes);
-        if (e != cudaSuccess) return e;
-        ptrs.push_back(q);
-        *p = static_cast<T *>(q);
-        return cudaSuccess;
-    }
-};
-
-
-}  // namespace
+using namespace wsh;
 
 extern "C" {
 
@@ -976,713 +787,6 @@ int ws_energy_noalloc(const float *u, const float *u_prev, const float *v, int n
             "ws_energy_noalloc");
     return WS_OK;
 }
-
-}  // extern "C"
-
-namespace {
-
-// Checks shared by ws_forward and ws_adjoint_gradient; selects the kernel and
-// makes sure the handle's adjoint scratch matches the run (N = nt_max steps).
-int adjoint_prepare(ws_t ws, const char *who, int *kern_out, ws::StreamTiling *tiling_out,
-                    AdjointCache **acp) {
-    if (!ws->vel_ok) return fail(WS_ERR_STATE, "%s: no valid velocity model", who);
-    if (ws->nrec == 0) return fail(WS_ERR_STATE, "%s: no receivers", who);
-    if (ws->storage != WS_STORAGE_FP32) return fail(WS_ERR_STATE, "%s: needs FP32 field storage", who);
-    const ws::Geom &g = ws->g;
-    const int N = ws->nt_max;
-    const int C = (int)std::ceil(std::sqrt((double)N));    // states per segment
-    const int nck = (N + C - 1) / C;                        // segments
-    int kern = WS_KERNEL_STREAM;
-    ws::StreamTiling tiling{};
-    int rc = prepare_fp32(ws, &kern, &tiling);
-    if (rc != WS_OK) return rc;
-    const bool maps = kern == WS_KERNEL_STREAM;
-    const size_t fb = field_bytes(g);
-    const size_t ncell = size_t(g.nx) * g.ny * g.nz;
-    const size_t ntr = size_t(ws->nrec) * N;
-    const cudaStream_t st = ws->stream;
-    AdjointCache *ac = ws->adj;
-    if (!ac || ac->N != N || ac->nrec != ws->nrec || ac->kern != kern ||
-        (maps && (ac->tx != ws->tiling.tx || ac->ty != ws->tiling.ty))) {
-        WS_CUDA(cudaStreamSynchronize(st), "ws_adjoint_gradient");
-        delete ws->adj;
-        ws->adj = nullptr;
-        ac = new (std::nothrow) AdjointCache();
-        if (!ac) return fail(WS_ERR_OOM, "ws_adjoint_gradient: host allocation failed");
-        ws->adj = ac;
-        auto grab = [&](auto **p, size_t bytes) -> cudaError_t {
-            void *q = nullptr;
-            cudaError_t e = cudaMalloc(&q, bytes);
-            if (e == cudaSuccess) {
-                ac->mem.push_back(q);
-                *p = static_cast<std::remove_reference_t<decltype(**p)> *>(q);
-            }
-            return e;
-        };
-        auto field = [&](MappedField *f) -> int {
-            WS_CUDA(grab(&f->p, fb), "cudaMalloc adjoint field");
-            WS_CUDA(cudaMemsetAsync(f->p, 0, fb, st), "zero adjoint field");
-            if (!maps) return WS_OK;
-            const int tx = ws->tiling.tx, ty = ws->tiling.ty;
-            int r2 = encode_map(&f->halo, f->p, g, tx + 2 * ws::kHalo, ty + 2 * ws::kHalo);
-            if (r2 == WS_OK) r2 = encode_map(&f->tile, f->p, g, tx, ty);
-            return r2;
-        };
-        // checkpoints (u^{jC}, u^{jC-1}), j = 1 .. nck-1; segment states; rho
-        ac->ck.assign(2 * size_t(nck - 1), nullptr);
-        for (auto &c : ac->ck) {
-            cudaError_t e = grab(&c, fb);
-            if (e != cudaSuccess) {
-                delete ws->adj;
-                ws->adj = nullptr;
-                return cuda_fail(e, "cudaMalloc checkpoint");
-            }
-        }
-        ac->lap.assign(C, nullptr);
-        cudaError_t e = cudaSuccess;
-        for (auto &f : ac->lap) {   // zeroed: the steps write the interior only
-            if (e == cudaSuccess) e = grab(&f, fb);
-            if (e == cudaSuccess) e = cudaMemsetAsync(f, 0, fb, st);
-        }
-        int r3 = e == cudaSuccess ? WS_OK : cuda_fail(e, "cudaMalloc adjoint field");
-        for (auto &f : ac->ring)
-            if (r3 == WS_OK) r3 = field(&f);
-        for (auto &f : ac->rho)
-            if (r3 == WS_OK) r3 = field(&f);
-        if (r3 == WS_OK) e = grab(&ac->acc, 2 * fb);   // float2 per cell, padded layout
-        if (r3 == WS_OK && e == cudaSuccess) e = grab(&ac->partials, sizeof(double) * (ws::residual_partial_count() + 1));
-        if (r3 == WS_OK && e == cudaSuccess) e = grab(&ac->r, sizeof(float) * ntr);
-        if (r3 == WS_OK && e == cudaSuccess) e = grab(&ac->dd, sizeof(float) * ntr);
-        if (r3 == WS_OK && e == cudaSuccess) e = grab(&ac->grad, sizeof(float) * ncell);
-        if (r3 == WS_OK && e == cudaSuccess) e = grab(&ac->rec, sizeof(int) * 3 * ws->nrec);
-        if (r3 != WS_OK || e != cudaSuccess) {
-            delete ws->adj;
-            ws->adj = nullptr;
-            return r3 != WS_OK ? r3 : cuda_fail(e, "cudaMalloc adjoint scratch");
-        }
-        ac->N = N;
-        ac->nrec = ws->nrec;
-        ac->kern = kern;
-        ac->tx = ws->tiling.tx;
-        ac->ty = ws->tiling.ty;
-    } else {
-    }
-    *kern_out = kern;
-    *tiling_out = tiling;
-    *acp = ac;
-    return WS_OK;
-}
-
-// The forward run from rest over N steps: traces recorded, checkpoint pairs
-// (u^{jC}, u^{jC-1}) saved; the cache then holds this model version's run.
-int adjoint_forward(ws_t ws, AdjointCache *ac, int kern, const ws::StreamTiling &tiling) {
-    const ws::Geom &g = ws->g;
-    const int N = ws->nt_max;
-    const int C = (int)std::ceil(std::sqrt((double)N));
-    const size_t fb = field_bytes(g);
-    const size_t ntr = size_t(ws->nrec) * N;
-    const cudaStream_t st = ws->stream;
-    std::vector<float *> &ck = ac->ck;
-    int rc = WS_OK;
-    ac->fwd_valid = false;
-    for (int b = 0; b < 2; ++b) WS_CUDA(cudaMemsetAsync(ws->buf[b], 0, fb, st), "zero fields");
-    WS_CUDA(cudaMemsetAsync(ws->traces, 0, sizeof(float) * ntr, st), "zero traces");
-    ws->step = 0;
-    ws->trace_start = 0;
-    ws::StepArgs a = base_args(ws);
-    for (int n = 0; n < N; ++n) {
-        if (n > 0 && n % C == 0) {
-            const int j = n / C;
-            WS_CUDA(cudaMemcpyAsync(ck[2 * (j - 1)], ws->buf[ws->cur], fb, cudaMemcpyDeviceToDevice, st),
-                    "save checkpoint");
-            WS_CUDA(cudaMemcpyAsync(ck[2 * (j - 1) + 1], ws->buf[1 - ws->cur], fb,
-                                    cudaMemcpyDeviceToDevice, st),
-                    "save checkpoint");
-        }
-        const int c = ws->cur;
-        rc = step_fp32(ws, a, kern, tiling, ws->buf[c], &ws->tmap_halo[c], ws->buf[1 - c],
-                       &ws->tmap_tile[1 - c], ws->buf[1 - c], n, true, true);
-        if (rc != WS_OK) return rc;
-        ws->cur = 1 - c;
-        ws->step++;
-    }
-
-    ac->fwd_valid = true;
-    ac->fwd_version = ws->model_version;
-    return WS_OK;
-}
-
-}  // namespace
-
-extern "C" {
-
-int ws_forward(ws_t ws) {
-    if (!ws) return fail(WS_ERR_BADARG, "ws_forward: NULL handle");
-    int kern = WS_KERNEL_STREAM;
-    ws::StreamTiling tiling{};
-    AdjointCache *ac = nullptr;
-    int rc = adjoint_prepare(ws, "ws_forward", &kern, &tiling, &ac);
-    if (rc != WS_OK) return rc;
-    return adjoint_forward(ws, ac, kern, tiling);
-}
-
-int ws_adjoint_gradient(ws_t ws, const float *data, int mode, float *grad_m, double *misfit,
-                        int on_device) {
-    if (!ws || !data || !grad_m) return fail(WS_ERR_BADARG, "ws_adjoint_gradient: NULL argument");
-    if (mode != WS_ADJ_DATA && mode != WS_ADJ_RESIDUAL)
-        return fail(WS_ERR_BADARG, "ws_adjoint_gradient: unknown mode %d", mode);
-    int kern = WS_KERNEL_STREAM;
-    ws::StreamTiling tiling{};
-    AdjointCache *ac = nullptr;
-    int rc = adjoint_prepare(ws, "ws_adjoint_gradient", &kern, &tiling, &ac);
-    if (rc != WS_OK) return rc;
-    const ws::Geom &g = ws->g;
-    const int N = ws->nt_max;
-    const int C = (int)std::ceil(std::sqrt((double)N));    // states per segment
-    const int nck = (N + C - 1) / C;                        // segments
-    const size_t fb = field_bytes(g);
-    const size_t ncell = size_t(g.nx) * g.ny * g.nz;
-    const size_t ntr = size_t(ws->nrec) * N;
-    const cudaStream_t st = ws->stream;
-    for (auto &f : ac->rho) WS_CUDA(cudaMemsetAsync(f.p, 0, fb, st), "zero adjoint field");
-    std::vector<float *> &ck = ac->ck;
-    std::vector<float *> &lap = ac->lap;
-    MappedField *ring = ac->ring;
-    MappedField *rho = ac->rho;
-    float2 *acc = ac->acc;
-    double *partials = ac->partials;
-    float *r = ac->r, *grad = on_device ? grad_m : ac->grad;
-    const float *d = data;
-    int *rec = ac->rec;
-    const int np = ws::residual_partial_count();
-    WS_CUDA(cudaMemsetAsync(acc, 0, 2 * fb, st), "zero gradient accumulator");
-    WS_CUDA(cudaMemcpyAsync(rec, ws->rec_ijk.data(), sizeof(int) * 3 * ws->nrec,
-                            cudaMemcpyHostToDevice, st),
-            "upload receivers");
-    if (!on_device) {
-        WS_CUDA(cudaMemcpyAsync(ac->dd, data, sizeof(float) * ntr, cudaMemcpyHostToDevice, st),
-                "upload observed data");
-        d = ac->dd;
-    }
-
-    // 1. forward from rest, recording the traces and the checkpoints; a
-    // residual given for the run that ws_forward left in the cache (same
-    // model version) needs no new forward run
-    if (!(mode == WS_ADJ_RESIDUAL && ac->fwd_valid && ac->fwd_version == ws->model_version)) {
-        rc = adjoint_forward(ws, ac, kern, tiling);
-        if (rc != WS_OK) return rc;
-    }
-    ws::StepArgs a = base_args(ws);
-
-    // 2. residual and misfit
-    WS_CUDA(ws::launch_residual(mode == WS_ADJ_DATA ? ws->traces : d,
-                                mode == WS_ADJ_DATA ? d : nullptr, (long long)ntr, r, partials,
-                                partials + np, st),
-            "residual kernels");
-    ws->launches += 2;
-
-    // 3. backward: rho^k, k = N .. 1, segment by segment, the segment's
-    // states recomputed from its checkpoint
-    int rc_cur = 0;   // rho[rc_cur] = rho^{k+1}, rho[1 - rc_cur] = rho^{k+2}
-    for (int j = nck - 1; j >= 0; --j) {
-        const int n0 = j * C, n1 = std::min(n0 + C, N);
-        // u^{n0}, u^{n0-1} into the ring, then steps n0 .. n1-1, each storing
-        // L u^n into lap[n - n0] (u^{n1} itself is not needed)
-        if (j == 0) {
-            WS_CUDA(cudaMemsetAsync(ring[0].p, 0, fb, st), "zero initial state");
-            WS_CUDA(cudaMemsetAsync(ring[1].p, 0, fb, st), "zero initial state");
-        } else {
-            WS_CUDA(cudaMemcpyAsync(ring[0].p, ck[2 * (j - 1)], fb, cudaMemcpyDeviceToDevice, st),
-                    "restore checkpoint");
-            WS_CUDA(cudaMemcpyAsync(ring[1].p, ck[2 * (j - 1) + 1], fb, cudaMemcpyDeviceToDevice, st),
-                    "restore checkpoint");
-        }
-        int uc = 0;   // ring[uc] = u^n
-        for (int t = 0; t < n1 - n0; ++t) {
-            MappedField &un = ring[uc], &um = ring[1 - uc];
-            a.lap = lap[t];
-            rc = step_fp32(ws, a, kern, tiling, un.p, &un.halo, um.p, &um.tile, um.p, n0 + t, true,
-                           false);
-            a.lap = nullptr;
-            if (rc != WS_OK) return rc;
-            uc = 1 - uc;
-        }
-        for (int k = n1; k > n0; --k) {
-            MappedField &r1 = rho[rc_cur], &r2 = rho[1 - rc_cur];
-            rc = step_fp32(ws, a, kern, tiling, r1.p, &r1.halo, r2.p, &r2.tile, r2.p, k, false,
-                           false);
-            if (rc != WS_OK) return rc;
-            rc_cur = 1 - rc_cur;   // rho[rc_cur] = rho^k
-            WS_CUDA(ws::launch_inject(rho[rc_cur].p, ws->w, ws->gx, ws->gy, ws->gz, g, rec,
-                                      ws->nrec, r, N, k - 1, st),
-                    "adjoint injection kernel");
-            ws::Sources src{};
-            sources_of_step(ws, k - 1, &src);
-            WS_CUDA(ws::launch_imaging(rho[rc_cur].p, lap[k - 1 - n0], g, src, ws->gx, ws->gy,
-                                       ws->gz, acc, st),
-                    "gradient imaging kernel");
-            ws->launches += 2;
-        }
-    }
-    const double hdt = ws->h / ws->dt;
-    WS_CUDA(ws::launch_finalize_gradient(acc, ws->w, g, hdt * hdt, grad, st),
-            "gradient finalize kernel");
-    ws->launches++;
-    if (!on_device)
-        WS_CUDA(cudaMemcpyAsync(grad_m, grad, sizeof(float) * ncell, cudaMemcpyDeviceToHost, st),
-                "copy gradient");
-    double J = 0.0;
-    WS_CUDA(cudaMemcpyAsync(&J, partials + np, sizeof(double), cudaMemcpyDeviceToHost, st),
-            "copy misfit");
-    WS_CUDA(cudaStreamSynchronize(st), "ws_adjoint_gradient");
-    if (misfit) *misfit = J;
-    unsigned status = 0;
-    WS_CUDA(cudaMemcpy(&status, ws->status, sizeof status, cudaMemcpyDeviceToHost),
-            "ws_adjoint_gradient");
-    if (status & ws::kStatusTimeout) {
-        WS_CUDA(cudaMemset(ws->status, 0, sizeof(unsigned)), "ws_adjoint_gradient");
-        return fail(WS_ERR_TIMEOUT, "a bounded device wait ran out in a step kernel");
-    }
-    return WS_OK;
-}
-
-int ws_autotune(ws_t ws, int *tile_x, int *tile_y, int *zblock) {
-    if (!ws) return fail(WS_ERR_BADARG, "ws_autotune: NULL handle");
-    if (!ws->vel_ok) return fail(WS_ERR_STATE, "ws_autotune: no valid velocity model");
-    if (ws->storage != WS_STORAGE_FP32)
-        return fail(WS_ERR_STATE, "ws_autotune: tunes the FP32 streaming kernel only");
-    const ws::Geom &g = ws->g;
-    ws::StreamTiling best{0, 0, 0};
-    {
-        std::lock_guard<std::mutex> lock(g_tune_mutex);
-        auto it = g_tune_cache.find(std::make_tuple(g.nx, g.ny, g.nz));
-        if (it != g_tune_cache.end()) best = it->second;
-    }
-    if (best.tx == 0) {
-        Scratch sc(ws->stream);
-        float *out = nullptr;
-        WS_CUDA(sc.alloc(&out, field_bytes(g)), "cudaMalloc tuning field");
-        cudaEvent_t e0, e1;
-        WS_CUDA(cudaEventCreate(&e0), "ws_autotune");
-        WS_CUDA(cudaEventCreate(&e1), "ws_autotune");
-        ws::StepArgs a = base_args(ws);
-        a.src.n = 0;
-        float best_ms = 1e30f;
-        const ws::StreamTiling keep = ws->tiling;
-        int rc = WS_OK;
-        for (const auto &tc : kTileCands) {
-            ws::StreamTiling t{tc[0], tc[1], 0};
-            if (!stream_fits(ws, t)) continue;
-            int slots = 0;
-            cudaError_t e = ws::stream_slots(t.tx, t.ty, false, &slots);
-            if (e != cudaSuccess) { rc = cuda_fail(e, "ws_autotune"); break; }
-            ws->tiling = t;
-            if ((rc = encode_maps(ws)) != WS_OK) break;
-            const long long tiles =
-                (long long)((g.nx + t.tx - 1) / t.tx) * ((g.ny + t.ty - 1) / t.ty);
-            for (int zb : zblock_candidates(g.nz, tiles, slots)) {
-                t.zb = zb;
-                const int c = ws->cur;
-                float ms = 0.f;
-                for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
-                    if (rep == 1) e = cudaEventRecord(e0, ws->stream);
-                    if (e == cudaSuccess)
-                        e = ws::launch_step_stream(&ws->tmap_halo[c], &ws->tmap_tile[1 - c],
-                                                   &ws->tmap_w, out, a, t, nullptr, nullptr,
-                                                   ws->stream);
-                    ws->launches++;
-                }
-                if (e == cudaSuccess) e = cudaEventRecord(e1, ws->stream);
-                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-                if (e != cudaSuccess) { rc = cuda_fail(e, "ws_autotune"); break; }
-                if (ms < best_ms) {
-                    best_ms = ms;
-                    best = t;
-                }
-            }
-            if (rc != WS_OK) break;
-        }
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
-        ws->tiling = keep;
-        if (rc != WS_OK) {
-            encode_maps(ws);
-            return rc;
-        }
-        if (best.tx != 0) {
-            std::lock_guard<std::mutex> lock(g_tune_mutex);
-            g_tune_cache[std::make_tuple(g.nx, g.ny, g.nz)] = best;
-        }
-    }
-    if (best.tx == 0) {   // no tile fits: the direct kernel
-        ws->kernel = WS_KERNEL_DIRECT;
-    } else {
-        ws->kernel = WS_KERNEL_STREAM;
-        ws->tiling = best;
-        int rc = encode_maps(ws);
-        if (rc != WS_OK) return rc;
-    }
-    if (tile_x) *tile_x = best.tx;
-    if (tile_y) *tile_y = best.ty;
-    if (zblock) *zblock = best.zb;
-    return WS_OK;
-}
-
-}  // extern "C"
-
-// ---------------------------------------------------------------- batches
-
-namespace {
-
-void batch_drop_graphs(ws_batch_t b) {
-    for (auto &kv : b->graphs) cudaGraphExecDestroy(kv.second);
-    b->graphs.clear();
-}
-
-void batch_free(ws_batch_t b) {
-    if (!b) return;
-    if (b->stream) cudaStreamSynchronize(b->stream);
-    batch_drop_graphs(b);
-    cudaFree(b->d_shots);
-    cudaFree(b->d_items);
-    cudaFree(b->d_src);
-    cudaFree(b->status);
-    for (cudaEvent_t e : {b->ev, b->t0, b->t1, b->t2})
-        if (e) cudaEventDestroy(e);
-    if (b->stream) cudaStreamDestroy(b->stream);
-    delete b;
-}
-
-// Configure every shot for tile tx x ty with z-blocks for m x slots items
-// (m = 0: each shot's default) and rebuild the item table: shots in order
-// of decreasing size, each shot's items block-major.
-int batch_configure(ws_batch_t b, int tx, int ty, int m) {
-    int slots = 0;
-    WS_CUDA(ws::stream_slots(tx, ty, true, &slots), "ws_batch_step");
-    const int n = (int)b->shots.size();
-    long long cells = 0;
-    for (ws_t ws : b->shots) cells += (long long)ws->g.nx * ws->g.ny * ws->g.nz;
-    std::vector<int> order(n);
-    for (int q = 0; q < n; ++q) order[q] = q;
-    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
-        const ws::Geom &gx = b->shots[x]->g, &gy = b->shots[y]->g;
-        return (long long)gx.nx * gx.ny * gx.nz > (long long)gy.nx * gy.ny * gy.nz;
-    });
-    std::vector<int2> items;
-    b->zb.assign(n, 0);
-    for (int q : order) {
-        ws_t ws = b->shots[q];
-        const ws::Geom &g = ws->g;
-        const long long tiles = (long long)((g.nx + tx - 1) / tx) * ((g.ny + ty - 1) / ty);
-        int zb = default_zblock(g.nz);
-        if (m > 0) {   // this shot's share of m waves, rounded down to whole blocks
-            const double share = double(g.nx) * g.ny * g.nz / double(cells);
-            const long long want = std::max<long long>(1, std::llround(m * slots * share));
-            const long long blocks = std::max<long long>(1, want / tiles);
-            zb = (int)std::min<long long>(g.nz, std::max<long long>(8, (g.nz + blocks - 1) / blocks));
-        }
-        b->zb[q] = zb;
-        if (ws->tiling.tx != tx || ws->tiling.ty != ty) {
-            ws->tiling.tx = tx;
-            ws->tiling.ty = ty;
-            int rc = encode_maps(ws);
-            if (rc != WS_OK) return rc;
-        }
-        int rc = build_rec_tiles(ws, ws::StreamTiling{tx, ty, zb});
-        if (rc != WS_OK) return rc;
-        const long long nit = tiles * ((g.nz + zb - 1) / zb);
-        for (long long l = 0; l < nit; ++l) items.push_back(make_int2(q, (int)l));
-    }
-    if ((long long)items.size() > INT32_MAX / 2)
-        return fail(WS_ERR_BADARG, "ws_batch_step: too many work items");
-    batch_drop_graphs(b);
-    cudaFree(b->d_items);
-    b->d_items = nullptr;
-    WS_CUDA(cudaMalloc(&b->d_items, sizeof(int2) * items.size()), "cudaMalloc batch items");
-    WS_CUDA(cudaMemcpyAsync(b->d_items, items.data(), sizeof(int2) * items.size(),
-                            cudaMemcpyHostToDevice, b->stream),
-            "upload batch items");
-    WS_CUDA(cudaStreamSynchronize(b->stream), "upload batch items");
-    b->nitems = (int)items.size();
-    b->tx = tx;
-    b->ty = ty;
-    b->cfg = ws_batch::Cand{tx, ty, m};
-    return WS_OK;
-}
-
-// Descriptors and source samples of the next nsteps steps.
-int batch_upload(ws_batch_t b, int nsteps) {
-    const int n = (int)b->shots.size();
-    // a shot may have been used on its own since the table was built: its
-    // tensor-map boxes and receiver table must match the batch's tile (a
-    // box larger than the kernel's ring slot would overrun shared memory)
-    for (int q = 0; q < n; ++q) {
-        ws_t ws = b->shots[q];
-        if (ws->tiling.tx != b->tx || ws->tiling.ty != b->ty) {
-            ws->tiling.tx = b->tx;
-            ws->tiling.ty = b->ty;
-            int rc = encode_maps(ws);
-            if (rc != WS_OK) return rc;
-        }
-        int rc = build_rec_tiles(ws, ws::StreamTiling{b->tx, b->ty, b->zb[q]});
-        if (rc != WS_OK) return rc;
-    }
-    size_t total = 0;
-    for (ws_t ws : b->shots) total += ws->src.size() * size_t(nsteps);
-    if (total > b->src_cap) {
-        cudaFree(b->d_src);
-        b->d_src = nullptr;
-        b->src_cap = 0;
-        WS_CUDA(cudaMalloc(&b->d_src, sizeof(ws::SourceSample) * std::max<size_t>(total, 1)),
-                "cudaMalloc batch sources");
-        b->src_cap = total;
-    }
-    std::vector<ws::SourceSample> src(total);
-    std::vector<ws::BatchShot> d(n);
-    size_t off = 0;
-    for (int q = 0; q < n; ++q) {
-        ws_t ws = b->shots[q];
-        ws::BatchShot &x = d[q];
-        for (int p = 0; p < 2; ++p) {
-            x.halo[p] = ws->tmap_halo[p];
-            x.tile[p] = ws->tmap_tile[p];
-            x.buf[p] = ws->buf[p];
-        }
-        x.w = ws->tmap_w;
-        x.gx = ws->gx;
-        x.gy = ws->gy;
-        x.gz = ws->gz;
-        x.nsrc = (int)ws->src.size();
-        x.src = b->d_src + off;
-        ws::Sources one{};
-        for (int t = 0; t < nsteps; ++t) {
-            sources_of_step(ws, ws->step + t, &one);
-            for (int k = 0; k < one.n; ++k) src[off + size_t(t) * one.n + k] = one.s[k];
-        }
-        off += size_t(x.nsrc) * nsteps;
-        const bool rec = ws->nrec > 0;
-        x.traces = rec ? ws->traces : nullptr;
-        x.rec_ptr = rec ? ws->rec_ptr : nullptr;
-        x.rec = rec ? ws->rec_entries : nullptr;
-        x.g = ws->g;
-        x.trace_col0 = ws->step - ws->trace_start;
-        x.nt_max = ws->nt_max;
-        x.cur0 = ws->cur;
-        x.zb = b->zb[q];
-        x.tiles_x = (ws->g.nx + b->tx - 1) / b->tx;
-        x.ntiles = x.tiles_x * ((ws->g.ny + b->ty - 1) / b->ty);
-    }
-    if (!b->d_shots)
-        WS_CUDA(cudaMalloc(&b->d_shots, sizeof(ws::BatchShot) * n), "cudaMalloc batch shots");
-    WS_CUDA(cudaMemcpyAsync(b->d_shots, d.data(), sizeof(ws::BatchShot) * n,
-                            cudaMemcpyHostToDevice, b->stream),
-            "upload batch shots");
-    if (total)
-        WS_CUDA(cudaMemcpyAsync(b->d_src, src.data(), sizeof(ws::SourceSample) * total,
-                                cudaMemcpyHostToDevice, b->stream),
-                "upload batch sources");
-    // the host vectors die here
-    WS_CUDA(cudaStreamSynchronize(b->stream), "upload batch shots");
-    return WS_OK;
-}
-
-ws::Coeffs step_coeffs() { return ws::Coeffs{(float)kW1, (float)kW2, (float)kW3, (float)kW4}; }
-
-// Run nsteps steps from the uploaded descriptors, as a CUDA graph.
-int batch_run(ws_batch_t b, int nsteps) {
-    const ws::Coeffs c = step_coeffs();
-    auto it = b->graphs.find(nsteps);
-    if (it == b->graphs.end()) {
-        int slots = 0;
-        WS_CUDA(ws::stream_slots(b->tx, b->ty, true, &slots), "ws_batch_step");
-        WS_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal),
-                "ws_batch_step capture");
-        cudaError_t e = cudaSuccess;
-        for (int t = 0; t < nsteps && e == cudaSuccess; ++t)
-            e = ws::launch_step_batch(b->d_shots, b->d_items, b->nitems, t, c, b->status, b->tx,
-                                      b->ty, b->stream);
-        cudaGraph_t graph = nullptr;
-        cudaError_t e2 = cudaStreamEndCapture(b->stream, &graph);
-        if (e == cudaSuccess) e = e2;
-        cudaGraphExec_t exec = nullptr;
-        if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
-        if (graph) cudaGraphDestroy(graph);
-        if (e != cudaSuccess) return cuda_fail(e, "ws_batch_step graph");
-        it = b->graphs.emplace(nsteps, exec).first;
-    }
-    WS_CUDA(cudaGraphLaunch(it->second, b->stream), "ws_batch_step graph launch");
-    b->launches += nsteps;
-    return WS_OK;
-}
-
-void batch_advance(ws_batch_t b, int nsteps) {
-    for (ws_t ws : b->shots) {
-        if (nsteps & 1) ws->cur = 1 - ws->cur;
-        ws->step += nsteps;
-    }
-}
-
-}  // namespace
-
-extern "C" {
-
-int ws_batch_create(ws_batch_t *out, int nshots, const ws_t *shots) {
-    if (!out) return fail(WS_ERR_BADARG, "ws_batch_create: out is NULL");
-    *out = nullptr;
-    if (nshots < 1 || !shots) return fail(WS_ERR_BADARG, "ws_batch_create: need nshots >= 1 handles");
-    for (int q = 0; q < nshots; ++q) {
-        if (!shots[q]) return fail(WS_ERR_BADARG, "ws_batch_create: handle %d is NULL", q);
-        for (int r = 0; r < q; ++r)
-            if (shots[r] == shots[q])
-                return fail(WS_ERR_BADARG, "ws_batch_create: handle %d appears twice", q);
-    }
-    ws_batch_t b = new (std::nothrow) ws_batch();
-    if (!b) return fail(WS_ERR_OOM, "ws_batch_create: host allocation failed");
-    b->shots.assign(shots, shots + nshots);
-    cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
-    for (cudaEvent_t *ev : {&b->ev, &b->t0, &b->t1, &b->t2})
-        if (e == cudaSuccess) e = cudaEventCreate(ev);
-    if (e == cudaSuccess) e = cudaMalloc(&b->status, sizeof(unsigned));
-    if (e == cudaSuccess) e = cudaMemsetAsync(b->status, 0, sizeof(unsigned), b->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
-    if (e != cudaSuccess) {
-        batch_free(b);
-        return cuda_fail(e, "ws_batch_create");
-    }
-    // online tuning candidates: every tile that fits every shot, z-blocks
-    // for 1, 2, 4, 8 x the resident CTAs and the per-shot default
-    for (const auto &tc : kTileCands) {
-        bool fits = true;
-        for (ws_t ws : b->shots) fits = fits && ws->g.nx >= tc[0] && ws->g.ny >= tc[1];
-        if (!fits) continue;
-        for (int m : {0, 1, 2, 3, 4, 6}) b->todo.push_back(ws_batch::Cand{tc[0], tc[1], m});
-    }
-    if (b->todo.empty()) {
-        batch_free(b);
-        return fail(WS_ERR_BADARG, "ws_batch_create: some shot is smaller than every tile "
-                                   "(needs nx >= 32 and ny >= 8)");
-    }
-    *out = b;
-    return WS_OK;
-}
-
-int ws_batch_destroy(ws_batch_t b) {
-    batch_free(b);
-    return WS_OK;
-}
-
-int ws_batch_set_tiling(ws_batch_t b, int tile_x, int tile_y, int zmul) {
-    if (!b) return fail(WS_ERR_BADARG, "ws_batch_set_tiling: NULL batch");
-    if (tile_x == 0 && tile_y == 0) {   // back to tuning
-        b->fixed = false;
-        return WS_OK;
-    }
-    if (!ws::stream_tiling_supported(tile_x, tile_y) || zmul < 0)
-        return fail(WS_ERR_BADARG, "ws_batch_set_tiling: unsupported tile %d x %d or zmul %d", tile_x,
-                    tile_y, zmul);
-    for (ws_t ws : b->shots)
-        if (ws->g.nx < tile_x || ws->g.ny < tile_y)
-            return fail(WS_ERR_BADARG, "ws_batch_set_tiling: a shot is smaller than the tile");
-    b->fixed = true;
-    b->best = ws_batch::Cand{tile_x, tile_y, zmul};
-    return WS_OK;
-}
-
-int ws_batch_get_tiling(ws_batch_t b, int *tile_x, int *tile_y, int *zmul) {
-    if (!b) return fail(WS_ERR_BADARG, "ws_batch_get_tiling: NULL batch");
-    if (tile_x) *tile_x = b->best.tx;
-    if (tile_y) *tile_y = b->best.ty;
-    if (zmul) *zmul = b->best.m;
-    return WS_OK;
-}
-
-int ws_batch_step(ws_batch_t b, int nsteps) {
-    if (!b) return fail(WS_ERR_BADARG, "ws_batch_step: NULL batch");
-    if (nsteps < 0) return fail(WS_ERR_BADARG, "ws_batch_step: nsteps must be >= 0");
-    for (size_t q = 0; q < b->shots.size(); ++q) {
-        ws_t ws = b->shots[q];
-        if (!ws->vel_ok) return fail(WS_ERR_STATE, "ws_batch_step: shot %zu has no velocity model", q);
-        if (ws->storage != WS_STORAGE_FP32)
-            return fail(WS_ERR_STATE, "ws_batch_step: shot %zu does not use FP32 storage", q);
-        if (ws->nrec > 0) {
-            const long long col = ws->step - ws->trace_start;
-            if (col < 0 || col + nsteps > ws->nt_max)
-                return fail(WS_ERR_STATE, "ws_batch_step: shot %zu can record %d steps from step "
-                                          "%lld, not steps %lld..%lld",
-                            q, ws->nt_max, ws->trace_start, ws->step, ws->step + nsteps - 1);
-        }
-    }
-    if (nsteps == 0) return WS_OK;
-    // order after the shots' own pending work
-    for (ws_t ws : b->shots) {
-        WS_CUDA(cudaEventRecord(b->ev, ws->stream), "ws_batch_step");
-        WS_CUDA(cudaStreamWaitEvent(b->stream, b->ev, 0), "ws_batch_step");
-    }
-    int done = 0, rc = WS_OK;
-    const ws::Coeffs c = step_coeffs();
-    // online tuning: each untried candidate takes two real steps (every
-    // tiling computes the same values); the second one is timed
-    while (!b->fixed && !b->tuned && nsteps - done >= 2 && rc == WS_OK) {
-        const ws_batch::Cand cd = b->todo.back();
-        b->todo.pop_back();
-        if ((rc = batch_configure(b, cd.tx, cd.ty, cd.m)) != WS_OK) break;
-        if ((rc = batch_upload(b, 2)) != WS_OK) break;
-        cudaError_t e = cudaEventRecord(b->t0, b->stream);
-        if (e == cudaSuccess)
-            e = ws::launch_step_batch(b->d_shots, b->d_items, b->nitems, 0, c, b->status, b->tx,
-                                      b->ty, b->stream);
-        if (e == cudaSuccess) e = cudaEventRecord(b->t1, b->stream);
-        if (e == cudaSuccess)
-            e = ws::launch_step_batch(b->d_shots, b->d_items, b->nitems, 1, c, b->status, b->tx,
-                                      b->ty, b->stream);
-        if (e == cudaSuccess) e = cudaEventRecord(b->t2, b->stream);
-        float ms = 0.f;
-        if (e == cudaSuccess) e = cudaEventSynchronize(b->t2);
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, b->t1, b->t2);
-        if (e != cudaSuccess) {
-            rc = cuda_fail(e, "ws_batch_step tuning");
-            break;
-        }
-        b->launches += 2;
-        batch_advance(b, 2);
-        done += 2;
-        if (ms < b->best_ms) {
-            b->best_ms = ms;
-            b->best = cd;
-        }
-        if (b->todo.empty()) b->tuned = true;
-    }
-    if (rc == WS_OK && done < nsteps) {
-        // the best candidate; while tuning is incomplete, 64 x 8 with 2 x CTAs items
-        const ws_batch::Cand want = b->best.tx ? b->best : ws_batch::Cand{64, 8, 2};
-        if (b->cfg.tx != want.tx || b->cfg.ty != want.ty || b->cfg.m != want.m)
-            rc = batch_configure(b, want.tx, want.ty, want.m);
-        if (rc == WS_OK) rc = batch_upload(b, nsteps - done);
-        if (rc == WS_OK) rc = batch_run(b, nsteps - done);
-        if (rc == WS_OK) batch_advance(b, nsteps - done);
-    }
-    // later work on each shot's stream follows the batch
-    cudaError_t e = cudaEventRecord(b->ev, b->stream);
-    for (ws_t ws : b->shots)
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(ws->stream, b->ev, 0);
-    if (rc == WS_OK && e != cudaSuccess) rc = cuda_fail(e, "ws_batch_step");
-    return rc;
-}
-
-int ws_batch_synchronize(ws_batch_t b) {
-    if (!b) return fail(WS_ERR_BADARG, "ws_batch_synchronize: NULL batch");
-    WS_CUDA(cudaStreamSynchronize(b->stream), "ws_batch_synchronize");
-    unsigned st = 0;
-    WS_CUDA(cudaMemcpy(&st, b->status, sizeof st, cudaMemcpyDeviceToHost), "ws_batch_synchronize");
-    if (st & ws::kStatusTimeout) {
-        WS_CUDA(cudaMemset(b->status, 0, sizeof(unsigned)), "ws_batch_synchronize");
-        return fail(WS_ERR_TIMEOUT, "a bounded device wait ran out in a batched step");
-    }
-    return WS_OK;
-}
-
-long long ws_batch_launch_count(ws_batch_t b) { return b ? b->launches : -1; }
 
 int ws_test_stall(ws_t ws, int item) {
     if (!ws) return fail(WS_ERR_BADARG, "ws_test_stall: NULL handle");
