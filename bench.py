@@ -425,7 +425,7 @@ def adjoint_report():
                         "true = layered + 10% Gaussian blob, start = layered",
             "gradient_s": min(times), "forward_s": fwd_s,
             "gradient_over_forward": min(times) / fwd_s,
-            "forward_rate": {"value": len(hs) * cells * w.nt / fwd_s / 1e9, "unit": UNIT},
+            "forward_rate": {"value": len(w.shots) * cells * w.nt / fwd_s / 1e9, "unit": UNIT},
             "misfit": J, "grad_max_abs": float(g.abs().max()),
             "tiling": {"tile": f"{tiling[0]}x{tiling[1]}", "zblock": tiling[2]},
             "passes": "forward (traces + sqrt(N) checkpoints), residual, then per segment a "
