@@ -245,8 +245,8 @@ int ws_forward(ws_t ws);
  * stays FP32. U and D share one power-of-two scale per step, picked on the
  * device from max|u^n| and the source amplitude so that the field's maximum
  * sits near 2^12 (16x under the FP16 limit). The current state is converted
- * (rounded once). 16-bit storage runs the streaming kernel with a 64x8 tile
- * and needs nx >= 64, ny >= 8, else BADARG. ws_read_field, ws_write_field
+ * (rounded once). 16-bit storage runs its own streaming kernel with a 64x16
+ * tile and needs nx >= 64, ny >= 16, else BADARG. ws_read_field, ws_write_field
  * and ws_energy convert to and from FP32 (ws_energy then uses the FP32
  * model). Relative L2 error against FP32 storage on the 1024^3 layered
  * survey, measured: FP16 8.6e-4, 3.0e-3, 4.3e-3 after 100, 500, 1000 steps;

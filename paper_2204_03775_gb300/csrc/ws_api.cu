@@ -147,25 +147,27 @@ void free_receivers(ws_t ws) {
     ws->rec_pidx = nullptr;
     ws->rec_ptr = nullptr;
     ws->rec_entries = nullptr;
-    ws->rec_tiling_tx = ws->rec_tiling_ty = 0;
+    ws->rec_tiling_tx = ws->rec_tiling_ty = ws->rec_tiling_rows = 0;
 }
 
 // Receiver table of the streaming kernels for tile t: per (tile, consumer
-// warp) a range of entries sorted by k.
-int build_rec_tiles(ws_t ws, const ws::StreamTiling &t) {
+// warp) a range of entries sorted by k. Thread owner = (row pair) * tx/4 + x
+// quad, lane = 4 * (row within the thread's rows) + x cell.
+int build_rec_tiles(ws_t ws, const ws::StreamTiling &t, int rows) {
     if (ws->nrec == 0) return WS_OK;
-    if (ws->rec_tiling_tx == t.tx && ws->rec_tiling_ty == t.ty) return WS_OK;
+    if (ws->rec_tiling_tx == t.tx && ws->rec_tiling_ty == t.ty && ws->rec_tiling_rows == rows)
+        return WS_OK;
     const int tiles_x = (ws->g.nx + t.tx - 1) / t.tx;
     const int tiles_y = (ws->g.ny + t.ty - 1) / t.ty;
-    const int warps = t.tx / 4 * t.ty / 32;   // consumer warps of a CTA
+    const int warps = t.tx / 4 * (t.ty / rows) / 32;   // consumer warps of a CTA
     const int ntiles = tiles_x * tiles_y * warps;   // (tile, warp) ranges
     std::vector<std::pair<int, ws::RecEntry>> e(ws->nrec);
     for (int r = 0; r < ws->nrec; ++r) {
         const int i = ws->rec_ijk[3 * r], j = ws->rec_ijk[3 * r + 1], k = ws->rec_ijk[3 * r + 2];
         const int tile = (j / t.ty) * tiles_x + (i / t.tx);
         const int li = i - (i / t.tx) * t.tx, lj = j - (j / t.ty) * t.ty;
-        const int owner = lj * (t.tx / 4) + li / 4;
-        e[r] = {tile * warps + owner / 32, ws::RecEntry{k, owner, li % 4, r}};
+        const int owner = (lj / rows) * (t.tx / 4) + li / 4;
+        e[r] = {tile * warps + owner / 32, ws::RecEntry{k, owner, (lj % rows) * 4 + li % 4, r}};
     }
     std::stable_sort(e.begin(), e.end(), [](const auto &x, const auto &y) {
         return x.first != y.first ? x.first < y.first : x.second.k < y.second.k;
@@ -194,6 +196,7 @@ int build_rec_tiles(ws_t ws, const ws::StreamTiling &t) {
     WS_CUDA(cudaStreamSynchronize(ws->stream), "upload receiver table");
     ws->rec_tiling_tx = t.tx;
     ws->rec_tiling_ty = t.ty;
+    ws->rec_tiling_rows = rows;
     return WS_OK;
 }
 
@@ -642,7 +645,7 @@ int ws_step(ws_t ws, int nsteps) {
         tiling.tx = kTile16X;
         tiling.ty = kTile16Y;
         tiling.zb = ws->tiling.zb > 0 ? ws->tiling.zb : default_zblock(ws->g.nz);
-        int rc = build_rec_tiles(ws, tiling);
+        int rc = build_rec_tiles(ws, tiling, kRows16);
         if (rc != WS_OK) return rc;
         if (!ws->w16_ok) {
             WS_CUDA(ws::launch_model16(ws->w, ws->w16, ws->g, ws->stream), "16-bit model");

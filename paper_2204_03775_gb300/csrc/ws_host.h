@@ -75,7 +75,7 @@ struct ws_handle {
     long long *rec_pidx = nullptr;       // direct path
     int *rec_ptr = nullptr;              // streaming path: per-tile ranges
     ws::RecEntry *rec_entries = nullptr;
-    int rec_tiling_tx = 0, rec_tiling_ty = 0;
+    int rec_tiling_tx = 0, rec_tiling_ty = 0, rec_tiling_rows = 0;
 
     int kernel = WS_KERNEL_AUTO;
     ws::StreamTiling tiling{64, 8, 0};
@@ -147,14 +147,15 @@ int default_zblock(const ws::Geom &g, int tx, int ty);
 // Choose the kernel for the next steps; fills *tiling for the streaming one.
 int pick_kernel(ws_t ws, ws::StreamTiling *tiling);
 void free_receivers(ws_t ws);
-// Receiver table of the streaming kernels for tile t.
-int build_rec_tiles(ws_t ws, const ws::StreamTiling &t);
+// Receiver table of the streaming kernels for tile t, whose consumer threads
+// own 4 x-cells of `rows` consecutive rows (FP32 kernels 1, 16-bit kernel 2).
+int build_rec_tiles(ws_t ws, const ws::StreamTiling &t, int rows = 1);
 // Unpadded [nz][ny][nx] user array <-> interior of a padded field.
 int copy_in(ws_t ws, float *dst, const float *src, int on_device);
 int copy_out(ws_t ws, float *dst, const float *src, int on_device);
 int upload_profiles(ws_t ws);
 // The tile of the 16-bit streaming kernel.
-constexpr int kTile16X = 64, kTile16Y = 8;
+constexpr int kTile16X = 64, kTile16Y = 16, kRows16 = 2;
 int encode_maps16(ws_t ws);
 int encode_state16(ws_t ws);
 int decode_state16(ws_t ws);

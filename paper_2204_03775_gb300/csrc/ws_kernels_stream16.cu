@@ -21,13 +21,15 @@
 // buffer: neighbours still read U); D is updated in place (only the thread
 // that computes a cell reads its D).
 //
-// Decoding, not memory, limits a 16-bit stencil: reading the x/y neighbours
-// straight from ring A decodes every halo value about five times (once per
-// thread that needs it). Instead the consumer warps decode each plane's halo
-// tile once into an FP32 staging tile (double-buffered), agree at a named
-// barrier that also ANDs their "no wait failed" flags (so a bounded wait
-// that gives up stops every consumer warp at the same plane), and read the
-// neighbours from the staging tile with the FP32 kernel's 128-bit loads.
+// Instruction issue, not memory, limits a 16-bit stencil, so every value is
+// decoded once: a thread decodes its own cells of plane k+4 into its register
+// queue, and at plane k writes them (FP32) into a double-buffered staging
+// tile; the cells around the tile that the star stencil reads (not the
+// corners) are decoded into the same tile by one unit of work per thread.
+// The consumer warps then agree at a named barrier that also ANDs their "no
+// wait failed" flags (so a bounded wait that gives up stops every consumer
+// warp at the same plane) and read their x/y neighbours from the staging tile
+// with 128-bit loads. Each thread computes 4 x-cells of two rows.
 //
 // One power-of-two scale per step for U' and D' (|d| <= |u^{n+1}| + |u^n|,
 // so the same exponent bounds both): stored values are value * 2^e, with e
@@ -36,21 +38,19 @@
 // 2^12, 16x below the FP16 maximum; exponents and maxima live in a 4-slot
 // ring (Scale16) indexed by step, so no host synchronization is needed.
 //
-// Decoding is exact and cheap: BF16 is the upper half of an FP32; for FP16,
-// ((h & 0x7fff) << 13) | (sign << 16) read as an FP32 is the FP16 value times
-// 2^-112 (normal and subnormal alike). The kernel computes on these "raw"
-// values: every input of one field carries the same power-of-two factor, the
-// model's factor is folded into the stencil weights, and the factors meet in
-// exact power-of-two multiplies. Results are rounded to 16 bits once, when
-// stored.
+// Decoding is exact and cheap: BF16 is the upper half of an FP32 (one shift
+// or mask), FP16 goes through the hardware conversion (one instruction per
+// value, measured 6% faster than rebuilding the bits with integer logic). The
+// kernel computes on the stored values: every input of one field carries the
+// same power-of-two factor, the model's factor 2^kW16Exp is folded into the
+// stencil weights, and the factors meet in exact power-of-two multiplies.
+// Results are rounded to 16 bits once, when stored.
 #include <climits>
 
 #include "ws_ptx.cuh"
 
 namespace ws {
 namespace {
-
-constexpr int kUnroll16 = 3;
 
 // 64-bit shared load (4 x 16-bit), kept whole.
 __device__ __forceinline__ uint2 lds2u(const uint16_t *p) {
@@ -59,8 +59,17 @@ __device__ __forceinline__ uint2 lds2u(const uint16_t *p) {
     return v;
 }
 
+// FP16 -> FP32 of the two halves of a word (exact, subnormals included).
+__device__ __forceinline__ float2 f16x2_to_f32(unsigned w) {
+    float2 r;
+    asm("{\n\t.reg .b16 l, h;\n\tmov.b32 {l, h}, %2;\n\t"
+        "cvt.f32.f16 %0, l;\n\tcvt.f32.f16 %1, h;\n\t}"
+        : "=f"(r.x), "=f"(r.y)
+        : "r"(w));
+    return r;
+}
+
 struct Bf16Fmt {
-    static constexpr int kRawExp = 0;  // raw = stored value * 2^kRawExp
     static __device__ __forceinline__ float4 decode(uint2 v) {
         return make_float4(__uint_as_float(v.x << 16), __uint_as_float(v.x & 0xffff0000u),
                            __uint_as_float(v.y << 16), __uint_as_float(v.y & 0xffff0000u));
@@ -74,15 +83,9 @@ struct Bf16Fmt {
 };
 
 struct Fp16Fmt {
-    static constexpr int kRawExp = -112;
-    static __device__ __forceinline__ float lo(unsigned w) {
-        return __uint_as_float(((w & 0x7fffu) << 13) | ((w & 0x8000u) << 16));
-    }
-    static __device__ __forceinline__ float hi(unsigned w) {
-        return __uint_as_float(((w >> 3) & 0x0fffe000u) | (w & 0x80000000u));
-    }
     static __device__ __forceinline__ float4 decode(uint2 v) {
-        return make_float4(lo(v.x), hi(v.x), lo(v.y), hi(v.y));
+        const float2 a = f16x2_to_f32(v.x), b = f16x2_to_f32(v.y);
+        return make_float4(a.x, a.y, b.x, b.y);
     }
     static __device__ __forceinline__ uint2 encode(float4 f) {
         uint2 r;
@@ -92,17 +95,14 @@ struct Fp16Fmt {
     }
 };
 
-// The model: FP16 of positive numbers, raw = value * 2^-112 (no sign bit).
-__device__ __forceinline__ float4 decode_w16(uint2 v) {
-    return make_float4(__uint_as_float((v.x << 13) & 0x0fffe000u),
-                       __uint_as_float((v.x >> 3) & 0x0fffe000u),
-                       __uint_as_float((v.y << 13) & 0x0fffe000u),
-                       __uint_as_float((v.y >> 3) & 0x0fffe000u));
-}
-
+// Two rows per thread: a consumer thread computes the 4 x-cells i..i+3 of the
+// rows j and j+1, so the per-plane costs of a thread (ring waits, barrier,
+// loads of the x neighbours, bookkeeping) are spread over 8 cells and the y
+// neighbours rows j-4..j-1 and j+2..j+5 serve both rows.
 template <int TX, int TY, int NA, int NB>
 struct Cfg16 {
-    static constexpr int kConsumers = (TX / 4) * TY;
+    static constexpr int kCols = TX / 4;               // threads across a row
+    static constexpr int kConsumers = kCols * (TY / 2);
     static constexpr int kThreads = kConsumers + 32;
     static constexpr int kLead = 8;                    // halo box starts 8 cells left: 16-byte x
     static constexpr int kRowW = TX + 2 * kLead;       // elements per ring-A row
@@ -112,16 +112,33 @@ struct Cfg16 {
     static constexpr int kTile = TX * TY;
     static constexpr int kSlotB = 2 * kTile;           // D tile, then W tile (16-bit elements)
     static constexpr unsigned kSlotBBytes = kSlotB * 2u;
-    static constexpr int kChunks = kSlotA / 4;         // 64-bit chunks of a ring-A slot
-    static constexpr size_t kStageBytes = size_t(kSlotA) * 4u;   // one FP32 staging tile
+    // FP32 staging tile: columns i0-4 .. i0+TX+3, rows j0-4 .. j0+TY+3 (the
+    // four corner blocks are never read by the star stencil and stay unset)
+    static constexpr int kSW = TX + 2 * kHalo;
+    static constexpr int kStage = kSW * kRows;
+    // halo units decoded per plane: TX units of 8 cells in the 8 bands above
+    // and below the tile (threads 0..TX-1), 2*TY units of 4 cells beside it
+    // (threads kSide0..), whole warps of one kind
+    static constexpr int kBandUnits = TX;
+    static constexpr int kSide0 = (kBandUnits + 31) / 32 * 32;
     static_assert(kConsumers % 32 == 0, "whole consumer warps");
+    static_assert(TX % 64 == 0 && TY % 2 == 0, "64-wide tiles, row pairs");
+    static_assert(kSide0 + 2 * TY <= kConsumers, "one halo unit per consumer thread at most");
     static_assert((NA & (NA - 1)) == 0 && NA >= 8 && (NB & (NB - 1)) == 0 && NB >= 2, "rings");
-    static_assert(kSlotABytes % 128 == 0 && kSlotBBytes % 128 == 0, "slots stay 128-byte aligned");
+    static_assert(kSlotABytes % 128 == 0 && kSlotBBytes % 128 == 0 && (kStage * 4) % 128 == 0,
+                  "slots stay 128-byte aligned");
     static constexpr size_t kSmem =
-        2 * kStageBytes + size_t(NA) * kSlotABytes + size_t(NB) * kSlotBBytes;
+        size_t(2 * kStage) * 4u + size_t(NA) * kSlotABytes + size_t(NB) * kSlotBBytes;
 };
 
-// 128-bit shared store.
+// 128-bit shared loads and stores.
+__device__ __forceinline__ uint4 lds4u(const uint16_t *p) {
+    uint4 v;
+    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "r"(smem_addr(p)));
+    return v;
+}
 __device__ __forceinline__ void sts4(float *p, float4 v) {
     asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(smem_addr(p)), "f"(v.x),
                  "f"(v.y), "f"(v.z), "f"(v.w)
@@ -166,31 +183,75 @@ __device__ __forceinline__ int scale_exponent(float a) {
     return max(-100, min(100, 12 - k));
 }
 
+// Receivers of a two-row thread: RecEntry.lane = 4 * row + x cell. Lane q of
+// the warp takes entry cur + q, fetches the owner's 8 values by shuffle and
+// stores the one it names.
+__device__ __forceinline__ void record_plane2(const float4 (&out)[2], float scale, int k, int *rcur,
+                                              int rend, int *rnext_k, const RecEntry *rec,
+                                              float *traces, int nt_max, long long trace_step) {
+    const int lane = threadIdx.x & 31;
+    int cur = *rcur;
+    for (;;) {
+        const int idx = cur + lane;
+        RecEntry e{INT_MAX, 0, 0, 0};
+        if (idx < rend) e = rec[idx];
+        const bool take = e.k == k;
+        const int src = e.owner & 31;
+        float v[8];
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            v[4 * r + 0] = __shfl_sync(0xffffffffu, out[r].x, src);
+            v[4 * r + 1] = __shfl_sync(0xffffffffu, out[r].y, src);
+            v[4 * r + 2] = __shfl_sync(0xffffffffu, out[r].z, src);
+            v[4 * r + 3] = __shfl_sync(0xffffffffu, out[r].w, src);
+        }
+        if (take) {
+            float x = v[0];
+#pragma unroll
+            for (int l = 1; l < 8; ++l)
+                if (e.lane == l) x = v[l];
+            traces[(long long)e.r * nt_max + trace_step] = x * scale;
+        }
+        const int n = __popc(__ballot_sync(0xffffffffu, take));
+        cur += n;
+        if (n < 32) break;
+    }
+    *rcur = cur;
+    *rnext_k = cur < rend ? rec[cur].k : INT_MAX;
+}
+
 struct Walk16 {
-    float4 q[9];        // raw u^n of planes k-4 .. k+4 (rotated)
+    float4 q[9][2];     // u^n (stored units) of planes k-4 .. k+4, rows j and j+1 (rotated)
     float gzb[3];       // z taper of planes k, k+1, k+2 (rotated)
-    float4 gxy;
-    uint16_t *out_k;    // U' of plane k; D of plane k is at out_k + d_delta
-    int nvalid;
+    float4 gxy[2];
+    uint16_t *out_k;    // U' of (i, j, k); D of it at out_k + d_delta, row j+1 one pitch on
+    int nvalid;         // valid x cells of the rows (0: none)
+    bool row1;          // row j+1 inside the grid
     int rcur, rend, rnext_k;
     unsigned src_mask;
     unsigned gAw, gAr, gB;
-    float amax;         // running max |u~| in raw u^n units
+    float amax;         // running max |u~| in stored units
     bool ok;
 };
 
-template <class Fmt, int TX, int TY, int NA, int NB>
+// A thread's halo unit: ring-A element offset, staging offset, kind (0 none,
+// 1 eight cells of a band row, 2 four cells beside the tile).
+struct Halo {
+    int src, dst, kind;
+};
+
+template <class Fmt, int TX, int TY, int NA, int NB, int NU>
 struct Kern16 {
     using Cfg = Cfg16<TX, TY, NA, NB>;
     using R = Rings<NA, NB>;
 
     // factors of one launch (uniform)
     struct Factors {
-        Coeffs c;       // stencil weights times 2^(112 - kW16Exp): absorbs the model's factor
-        float wtrue;    // raw W -> (V dt/h)^2
-        float amp2r;    // source amplitude (h^2 s) -> raw U units
-        float ro;       // raw u~ and u~ - u -> stored U' and D' values
-        int r2t;        // raw U units -> true units: times 2^r2t
+        Coeffs c;       // stencil weights times 2^-kW16Exp: absorbs the model's factor
+        float wtrue;    // stored W -> (V dt/h)^2
+        float amp2r;    // source amplitude (h^2 s) -> stored U units
+        float ro;       // u~ and u~ - u (stored U units) -> stored U' and D' values
+        int r2t;        // stored U units -> true units: times 2^r2t
     };
 
     static __device__ __forceinline__ bool produce_a(R &rg, uint16_t *ringA, const Maps16 &mp,
@@ -249,55 +310,32 @@ struct Kern16 {
         }
     }
 
+    static __device__ __forceinline__ Halo halo_unit(int tid) {
+        Halo h{0, 0, 0};
+        if (tid < Cfg::kBandUnits) {
+            const int per_row = TX / 8;
+            const int band = tid / per_row, n = tid - band * per_row;
+            const int y = band < kHalo ? band : TY + band;      // rows 0..3, TY+4..TY+7
+            const int c = kHalo + 8 * n;                          // staging column
+            h = Halo{y * Cfg::kRowW + c + (Cfg::kLead - kHalo), y * Cfg::kSW + c, 1};
+        } else if (tid >= Cfg::kSide0 && tid < Cfg::kSide0 + 2 * TY) {
+            const int v = tid - Cfg::kSide0;
+            const int y = kHalo + (v >> 1);
+            const int c = (v & 1) ? TX + kHalo : 0;
+            h = Halo{y * Cfg::kRowW + c + (Cfg::kLead - kHalo), y * Cfg::kSW + c, 2};
+        }
+        return h;
+    }
+
+    // u~ (stored units) of one row's 4 cells: the tapered leapfrog update of the FP32
+    // kernels, in their operation order. yp/ym: rows j+m / j-m of this row.
     template <int RQ>
-    static __device__ __forceinline__ void plane_step(Walk16 &wk, R &rg, const uint16_t *ringA,
-                                                      const uint16_t *ringB, float *stage,
-                                                      const StepArgs &a,
-                                                      const Factors &fc, long long d_delta,
-                                                      const Item &it, int k, int i, int j,
-                                                      int offA, int offB, const RecEntry *rec) {
-#define QI(m) ((RQ + (m)) % 9)
-#define BI(d) ((RQ + (d)) % 3)
-        {
-            const int slot = wk.gAw & (NA - 1);
-            wk.ok = wk.ok && wait_phase(&rg.fullA[slot], (wk.gAw / NA) & 1u, &rg.abort, a.status);
-            wk.q[QI(8)] = Fmt::decode(lds2u(ringA + slot * Cfg::kSlotA + offA));
-            ++wk.gAw;
-        }
-        const int sb = wk.gB & (NB - 1);
-        wk.ok = wk.ok && wait_phase(&rg.fullB[sb], (wk.gB / NB) & 1u, &rg.abort, a.status);
-        const uint16_t *tb = ringB + sb * Cfg::kSlotB;
-        const float4 dc = Fmt::decode(lds2u(tb + offB));
-        const float4 wr = decode_w16(lds2u(tb + Cfg::kTile + offB));
-        warp_arrive(&rg.emptyB[sb]);
-        ++wk.gB;
-
-        if (k + 2 < it.z1) wk.gzb[BI(2)] = __ldg(a.gz + k + 2);
-
-        // plane k's halo tile (waited for four planes ago), decoded once into
-        // this plane's staging tile; then every consumer agrees before reading
-        {
-            const uint16_t *src = ringA + (wk.gAr & (NA - 1)) * Cfg::kSlotA;
-            float *dst = stage + (k & 1) * Cfg::kSlotA;
-#pragma unroll
-            for (int c = threadIdx.x; c < Cfg::kChunks; c += Cfg::kConsumers)
-                sts4(dst + 4 * c, Fmt::decode(lds2u(src + 4 * c)));
-        }
-        wk.ok = consumers_all(wk.ok, Cfg::kConsumers);
-        warp_arrive(&rg.emptyA[wk.gAr & (NA - 1)]);
-        ++wk.gAr;
-
-        const float *row = stage + (k & 1) * Cfg::kSlotA + offA;
-        const float4 xl = lds4(row - 4);
-        const float4 xc = wk.q[QI(4)];
-        const float4 xr = lds4(row + 4);
-        float4 yp[4], ym[4];
-#pragma unroll
-        for (int m = 1; m <= 4; ++m) {
-            yp[m - 1] = lds4(row + m * Cfg::kRowW);
-            ym[m - 1] = lds4(row - m * Cfg::kRowW);
-        }
-
+    static __device__ __forceinline__ float4 update_row(const Walk16 &wk, int r, const float4 &xl,
+                                                        const float4 &xr, const float4 (&yp)[4],
+                                                        const float4 (&ym)[4], const float4 &dc,
+                                                        const float4 &wr, float gzk,
+                                                        const Factors &fc) {
+        const float4 xc = wk.q[(RQ + 4) % 9][r];
         const float e[12] = {xl.x, xl.y, xl.z, xl.w, xc.x, xc.y, xc.z, xc.w,
                              xr.x, xr.y, xr.z, xr.w};
         float2 sx[2][5];
@@ -313,8 +351,6 @@ struct Kern16 {
                 sx[p][m] = make_float2(e[4 + l0 + m] + e[4 + l0 - m], e[4 + l1 + m] + e[4 + l1 - m]);
             }
         }
-
-        const float gzk = wk.gzb[BI(0)];
         float2 o[2];
 #pragma unroll
         for (int p = 0; p < 2; ++p) {
@@ -322,7 +358,8 @@ struct Kern16 {
 #pragma unroll
             for (int m = 1; m <= 4; ++m) {
                 const float2 sy = add2(pair(yp[m - 1], p), pair(ym[m - 1], p));
-                const float2 sz = add2(pair(wk.q[QI(4 + m)], p), pair(wk.q[QI(4 - m)], p));
+                const float2 sz = add2(pair(wk.q[(RQ + 4 + m) % 9][r], p),
+                                       pair(wk.q[(RQ + 4 - m + 9) % 9][r], p));
                 s[m] = add2(add2(sx[p][m], sy), sz);
             }
             const float2 uc = pair(xc, p);
@@ -332,67 +369,189 @@ struct Kern16 {
             lap = fma2(splat(fc.c.c2), fma2(splat(-6.0f), uc, s[2]), lap);
             lap = fma2(splat(fc.c.c1), fma2(splat(-6.0f), uc, s[1]), lap);
             const float2 um = add2(uc, mul2(splat(-1.0f), pair(dc, p)));     // u^{n-1}
-            const float2 gd = mul2(pair(wk.gxy, p), splat(gzk));
-            const float2 ngd = mul2(pair(wk.gxy, p), splat(-gzk));           // -gd, exactly
+            const float2 gd = mul2(pair(wk.gxy[r], p), splat(gzk));
+            const float2 ngd = mul2(pair(wk.gxy[r], p), splat(-gzk));        // -gd, exactly
             const float2 t = fma2(pair(wr, p), lap, fma2(splat(2.0f), uc, mul2(ngd, um)));
-            o[p] = mul2(gd, t);                                              // u~ (raw)
+            o[p] = mul2(gd, t);                                              // u~
         }
-        float4 un = make_float4(o[0].x, o[0].y, o[1].x, o[1].y);
+        return make_float4(o[0].x, o[0].y, o[1].x, o[1].y);
+    }
+
+    template <int RQ>
+    static __device__ __forceinline__ void plane_step(Walk16 &wk, R &rg, const uint16_t *ringA,
+                                                      const uint16_t *ringB, float *stage,
+                                                      const StepArgs &a, const Factors &fc,
+                                                      long long d_delta, const Halo &hu, int k,
+                                                      int i, int j, int offA, int offB, int offS,
+                                                      const RecEntry *rec) {
+        constexpr int Q8 = (RQ + 8) % 9, Q4 = (RQ + 4) % 9;
+        // plane k+4 of this thread's two rows -> the queue
+        {
+            const int slot = wk.gAw & (NA - 1);
+            wk.ok = wait_phase(&rg.fullA[slot], (wk.gAw / NA) & 1u, &rg.abort, a.status) && wk.ok;
+            const uint16_t *p = ringA + slot * Cfg::kSlotA + offA;
+            wk.q[Q8][0] = Fmt::decode(lds2u(p));
+            wk.q[Q8][1] = Fmt::decode(lds2u(p + Cfg::kRowW));
+            ++wk.gAw;
+        }
+        const int sb = wk.gB & (NB - 1);
+        wk.ok = wait_phase(&rg.fullB[sb], (wk.gB / NB) & 1u, &rg.abort, a.status) && wk.ok;
+        const uint16_t *tb = ringB + sb * Cfg::kSlotB + offB;
+        const float4 dc0 = Fmt::decode(lds2u(tb)), dc1 = Fmt::decode(lds2u(tb + TX));
+        const float4 wr0 = Fp16Fmt::decode(lds2u(tb + Cfg::kTile));
+        const float4 wr1 = Fp16Fmt::decode(lds2u(tb + Cfg::kTile + TX));
+        warp_arrive(&rg.emptyB[sb]);
+        ++wk.gB;
+
+        wk.gzb[(RQ + 2) % 3] = __ldg(a.gz + min(k + 2, a.g.nz - 1));   // past nz: unused
+
+        // staging tile of plane k: this thread's own two rows (decoded four
+        // planes ago), and its halo unit from the ring; then every consumer
+        // agrees before anyone reads a neighbour
+        float *st = stage + (k & 1) * Cfg::kStage;
+        sts4(st + offS, wk.q[Q4][0]);
+        sts4(st + offS + Cfg::kSW, wk.q[Q4][1]);
+        {
+            const uint16_t *src = ringA + (wk.gAr & (NA - 1)) * Cfg::kSlotA + hu.src;
+            if (hu.kind == 1) {
+                const uint4 v = lds4u(src);
+                sts4(st + hu.dst, Fmt::decode(make_uint2(v.x, v.y)));
+                sts4(st + hu.dst + 4, Fmt::decode(make_uint2(v.z, v.w)));
+            } else if (hu.kind == 2) {
+                sts4(st + hu.dst, Fmt::decode(lds2u(src)));
+            }
+        }
+        wk.ok = consumers_all(wk.ok, Cfg::kConsumers);
+        warp_arrive(&rg.emptyA[wk.gAr & (NA - 1)]);
+        ++wk.gAr;
+
+        const float *row = st + offS;
+        const float4 xl0 = lds4(row - 4), xr0 = lds4(row + 4);
+        const float4 xl1 = lds4(row + Cfg::kSW - 4), xr1 = lds4(row + Cfg::kSW + 4);
+        // rows j-4..j-1 and j+2..j+5
+        float4 lm[4], lp[4];
+#pragma unroll
+        for (int m = 1; m <= 4; ++m) {
+            lm[m - 1] = lds4(row - m * Cfg::kSW);
+            lp[m - 1] = lds4(row + (m + 1) * Cfg::kSW);
+        }
+        const float gzk = wk.gzb[RQ % 3];
+        float4 un[2];
+        {
+            const float4 yp[4] = {wk.q[Q4][1], lp[0], lp[1], lp[2]};
+            un[0] = update_row<RQ>(wk, 0, xl0, xr0, yp, lm, dc0, wr0, gzk, fc);
+        }
+        {
+            const float4 ym[4] = {wk.q[Q4][0], lm[0], lm[1], lm[2]};
+            un[1] = update_row<RQ>(wk, 1, xl1, xr1, lp, ym, dc1, wr1, gzk, fc);
+        }
         if (wk.src_mask) {
             for (int qs = 0; qs < a.src.n; ++qs) {
                 const SourceSample &ss = a.src.s[qs];
-                if (((wk.src_mask >> qs) & 1u) && ss.k == k && ss.j == j) {
+                if (((wk.src_mask >> qs) & 1u) && ss.k == k) {
 #pragma unroll
-                    for (int l = 0; l < 4; ++l)
-                        if (ss.i == i + l)
-                            set_comp(un, l, fmaf(comp(wr, l) * fc.wtrue, ss.amp * fc.amp2r,
-                                                 comp(un, l)));
+                    for (int r = 0; r < 2; ++r) {
+                        if (ss.j != j + r) continue;
+                        const float4 &wr = r ? wr1 : wr0;
+#pragma unroll
+                        for (int l = 0; l < 4; ++l)
+                            if (ss.i == i + l)
+                                set_comp(un[r], l, fmaf(comp(wr, l) * fc.wtrue, ss.amp * fc.amp2r,
+                                                        comp(un[r], l)));
+                    }
                 }
             }
         }
-        // increments u~ - u (raw), then the stored values
-        const float2 d0 = add2(lo2(un), make_float2(-xc.x, -xc.y));
-        const float2 d1 = add2(hi2(un), make_float2(-xc.z, -xc.w));
+        // cells outside the grid have zero taper, so zero u~: no guard needed
+        wk.amax = fmaxf(wk.amax, fmaxf(fmaxf(fmaxf(fabsf(un[0].x), fabsf(un[0].y)),
+                                             fmaxf(fabsf(un[0].z), fabsf(un[0].w))),
+                                       fmaxf(fmaxf(fabsf(un[1].x), fabsf(un[1].y)),
+                                             fmaxf(fabsf(un[1].z), fabsf(un[1].w)))));
         if (wk.nvalid > 0) {
-            // columns past nx have zero taper and zero u: they add nothing here
-            wk.amax = fmaxf(wk.amax, fmaxf(fmaxf(fabsf(un.x), fabsf(un.y)),
-                                           fmaxf(fabsf(un.z), fabsf(un.w))));
-            const float2 su0 = mul2(lo2(un), splat(fc.ro)), su1 = mul2(hi2(un), splat(fc.ro));
-            const float2 sd0 = mul2(d0, splat(fc.ro)), sd1 = mul2(d1, splat(fc.ro));
-            store16(wk.out_k, Fmt::encode(make_float4(su0.x, su0.y, su1.x, su1.y)), wk.nvalid);
-            store16(wk.out_k + d_delta, Fmt::encode(make_float4(sd0.x, sd0.y, sd1.x, sd1.y)),
-                    wk.nvalid);
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                if (r == 1 && !wk.row1) break;
+                const float4 xc = wk.q[Q4][r];
+                // increments u~ - u, then the stored values
+                const float2 d0 = add2(lo2(un[r]), make_float2(-xc.x, -xc.y));
+                const float2 d1 = add2(hi2(un[r]), make_float2(-xc.z, -xc.w));
+                const float2 su0 = mul2(lo2(un[r]), splat(fc.ro));
+                const float2 su1 = mul2(hi2(un[r]), splat(fc.ro));
+                const float2 sd0 = mul2(d0, splat(fc.ro)), sd1 = mul2(d1, splat(fc.ro));
+                uint16_t *o = wk.out_k + r * a.g.pnx;
+                store16(o, Fmt::encode(make_float4(su0.x, su0.y, su1.x, su1.y)), wk.nvalid);
+                store16(o + d_delta, Fmt::encode(make_float4(sd0.x, sd0.y, sd1.x, sd1.y)),
+                        wk.nvalid);
+            }
         }
         wk.out_k += a.g.plane;
         if (k == wk.rnext_k) {
-            const float4 ut = make_float4(scale2(un.x, fc.r2t), scale2(un.y, fc.r2t),
-                                          scale2(un.z, fc.r2t), scale2(un.w, fc.r2t));
-            record_plane(ut, 1.0f, k, &wk.rcur, wk.rend, &wk.rnext_k, rec, a.traces, a.nt_max,
-                         a.trace_step);
+            float4 ut[2];
+#pragma unroll
+            for (int r = 0; r < 2; ++r)
+                ut[r] = make_float4(scale2(un[r].x, fc.r2t), scale2(un[r].y, fc.r2t),
+                                    scale2(un[r].z, fc.r2t), scale2(un[r].w, fc.r2t));
+            record_plane2(ut, 1.0f, k, &wk.rcur, wk.rend, &wk.rnext_k, rec, a.traces, a.nt_max,
+                          a.trace_step);
         }
-#undef QI
-#undef BI
+    }
+
+    // planes kb + RQ .. kb + NU - 1 of a group; false once the item ends
+    template <int RQ>
+    static __device__ __forceinline__ bool planes(Walk16 &wk, R &rg, const uint16_t *ringA,
+                                                  const uint16_t *ringB, float *stage,
+                                                  const StepArgs &a, const Factors &fc,
+                                                  long long d_delta, const Halo &hu,
+                                                  const Item &it, int kb, int i, int j, int offA,
+                                                  int offB, int offS, const RecEntry *rec) {
+        if constexpr (RQ < NU) {
+            if (kb + RQ >= it.z1) return false;
+            plane_step<RQ>(wk, rg, ringA, ringB, stage, a, fc, d_delta, hu, kb + RQ, i, j, offA,
+                           offB, offS, rec);
+            // wk.ok is the same in every consumer after the staging barrier
+            if (!wk.ok) return false;
+            return planes<RQ + 1>(wk, rg, ringA, ringB, stage, a, fc, d_delta, hu, it, kb, i, j,
+                                  offA, offB, offS, rec);
+        }
+        return true;
     }
 
     static __device__ __forceinline__ void rotate_queue(Walk16 &wk) {
-        float4 t[9];
+        if constexpr (NU % 9 != 0) {
+            float4 t[9][2];
 #pragma unroll
-        for (int m = 0; m < 9; ++m) t[m] = wk.q[(m + kUnroll16) % 9];
+            for (int m = 0; m < 9; ++m) {
+                t[m][0] = wk.q[(m + NU) % 9][0];
+                t[m][1] = wk.q[(m + NU) % 9][1];
+            }
 #pragma unroll
-        for (int m = 0; m < 9; ++m) wk.q[m] = t[m];
+            for (int m = 0; m < 9; ++m) {
+                wk.q[m][0] = t[m][0];
+                wk.q[m][1] = t[m][1];
+            }
+        }
+        if constexpr (NU % 3 != 0) {
+            const float t0 = wk.gzb[NU % 3], t1 = wk.gzb[(NU + 1) % 3], t2 = wk.gzb[(NU + 2) % 3];
+            wk.gzb[0] = t0;
+            wk.gzb[1] = t1;
+            wk.gzb[2] = t2;
+        }
     }
 
-    static __device__ void consumer(R &rg, const uint16_t *ringA, const uint16_t *ringB,
-                                    float *stage, uint16_t *u_out, long long d_delta,
+    static __device__ __forceinline__ void consumer(R &rg, const uint16_t *ringA,
+                                                    const uint16_t *ringB, float *stage,
+                                                    uint16_t *u_out, long long d_delta,
                                     const StepArgs &a, const Factors &fc, int zb, int tiles_x,
                                     int ntiles, int nitems, const int *rec_ptr,
                                     const RecEntry *rec, unsigned *amax_out) {
         const Geom &g = a.g;
         const int tid = threadIdx.x;
-        const int tx = tid % (TX / 4);
-        const int ty = tid / (TX / 4);
-        const int offA = (kHalo + ty) * Cfg::kRowW + Cfg::kLead + 4 * tx;
-        const int offB = ty * TX + 4 * tx;
+        const int tx = tid % Cfg::kCols;
+        const int py = tid / Cfg::kCols;
+        const int offA = (kHalo + 2 * py) * Cfg::kRowW + Cfg::kLead + 4 * tx;
+        const int offB = 2 * py * TX + 4 * tx;
+        const int offS = (kHalo + 2 * py) * Cfg::kSW + kHalo + 4 * tx;
+        const Halo hu = halo_unit(tid);
         Walk16 wk;
         wk.gAw = wk.gAr = wk.gB = 0;
         wk.ok = true;
@@ -400,16 +559,20 @@ struct Kern16 {
         for (int item = blockIdx.x; item < nitems && wk.ok; item += gridDim.x) {
             const Item it = item_of(item, tiles_x, ntiles, zb, g.nz, TX, TY);
             const int i = it.i0 + 4 * tx;
-            const int j = it.j0 + ty;
+            const int j = it.j0 + 2 * py;
             const bool col_ok = (j < g.ny) && (i < g.nx);
             wk.nvalid = col_ok ? min(4, g.nx - i) : 0;
-            wk.gxy = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (col_ok) {
-                const float gyj = a.gy[j];
-                wk.gxy.x = a.gx[i] * gyj;
-                if (wk.nvalid > 1) wk.gxy.y = a.gx[i + 1] * gyj;
-                if (wk.nvalid > 2) wk.gxy.z = a.gx[i + 2] * gyj;
-                if (wk.nvalid > 3) wk.gxy.w = a.gx[i + 3] * gyj;
+            wk.row1 = j + 1 < g.ny;
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                wk.gxy[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (col_ok && j + r < g.ny) {
+                    const float gyj = a.gy[j + r];
+                    wk.gxy[r].x = a.gx[i] * gyj;
+                    if (wk.nvalid > 1) wk.gxy[r].y = a.gx[i + 1] * gyj;
+                    if (wk.nvalid > 2) wk.gxy[r].z = a.gx[i + 2] * gyj;
+                    if (wk.nvalid > 3) wk.gxy[r].w = a.gx[i + 3] * gyj;
+                }
             }
             wk.src_mask = 0u;
             for (int qs = 0; qs < a.src.n; ++qs) {
@@ -428,13 +591,15 @@ struct Kern16 {
             wk.out_k = u_out + pidx(g, col_ok ? i : 0, col_ok ? j : 0, it.z0);
 #pragma unroll
             for (int d = 0; d < 2; ++d)
-                wk.gzb[d] = (it.z0 + d < it.z1) ? __ldg(a.gz + it.z0 + d) : 1.0f;
+                wk.gzb[d] = (it.z0 + d < g.nz) ? __ldg(a.gz + it.z0 + d) : 1.0f;
 
 #pragma unroll
             for (int m = 0; m < 2 * kHalo; ++m) {
                 const int slot = wk.gAw & (NA - 1);
                 wk.ok = wk.ok && wait_phase(&rg.fullA[slot], (wk.gAw / NA) & 1u, &rg.abort, a.status);
-                wk.q[m] = Fmt::decode(lds2u(ringA + slot * Cfg::kSlotA + offA));
+                const uint16_t *p = ringA + slot * Cfg::kSlotA + offA;
+                wk.q[m][0] = Fmt::decode(lds2u(p));
+                wk.q[m][1] = Fmt::decode(lds2u(p + Cfg::kRowW));
                 ++wk.gAw;
             }
 #pragma unroll
@@ -442,22 +607,17 @@ struct Kern16 {
                 warp_arrive(&rg.emptyA[wk.gAr & (NA - 1)]);
                 ++wk.gAr;
             }
-            // every consumer warp leaves together (the staging barrier needs all)
+            // every consumer leaves together (the staging barrier needs all)
             wk.ok = consumers_all(wk.ok, Cfg::kConsumers);
             if (!wk.ok) break;
 
-            for (int kb = it.z0; kb < it.z1; kb += kUnroll16) {
-#define WS_PLANE(RQ)                                                                           \
-    if (kb + (RQ) >= it.z1) break;                                                             \
-    plane_step<RQ>(wk, rg, ringA, ringB, stage, a, fc, d_delta, it, kb + (RQ), i, j, offA, offB, \
-                   rec);                                                                       \
-    if (!warp_all_ok(wk)) break;
-                WS_PLANE(0)
-                WS_PLANE(1)
-                WS_PLANE(2)
-#undef WS_PLANE
+            for (int kb = it.z0; kb < it.z1; kb += NU) {
+                if (!planes<0>(wk, rg, ringA, ringB, stage, a, fc, d_delta, hu, it, kb, i, j,
+                               offA, offB, offS, rec))
+                    break;
                 rotate_queue(wk);
             }
+            if (!wk.ok) break;
 #pragma unroll
             for (int m = 0; m < kHalo; ++m) {
                 warp_arrive(&rg.emptyA[wk.gAr & (NA - 1)]);
@@ -472,19 +632,19 @@ struct Kern16 {
     }
 };
 
-template <class Fmt, int TX, int TY, int NA, int NB, int MINB>
+template <class Fmt, int TX, int TY, int NA, int NB, int NU, int MINB>
 __global__ void __launch_bounds__(Cfg16<TX, TY, NA, NB>::kThreads, MINB)
     step_stream16_kernel(const __grid_constant__ Maps16 maps, uint16_t *__restrict__ u_out,
                          uint16_t *d_io, const __grid_constant__ StepArgs a,
                          Scale16 *__restrict__ sc, const long long step, const float src_hint,
                          const int zb, const int tiles_x, const int ntiles, const int nitems,
                          const int *__restrict__ rec_ptr, const RecEntry *__restrict__ rec) {
-    using K = Kern16<Fmt, TX, TY, NA, NB>;
+    using K = Kern16<Fmt, TX, TY, NA, NB, NU>;
     using Cfg = typename K::Cfg;
     extern __shared__ __align__(128) float smem16[];
     __shared__ Rings<NA, NB> rg;
     float *stage = smem16;
-    uint16_t *ringA = reinterpret_cast<uint16_t *>(smem16 + 2 * Cfg::kSlotA);
+    uint16_t *ringA = reinterpret_cast<uint16_t *>(smem16 + 2 * Cfg::kStage);
     uint16_t *ringB = ringA + NA * Cfg::kSlotA;
 
     // scale of this step: U, D of step n have e; U', D' get e_o
@@ -492,12 +652,12 @@ __global__ void __launch_bounds__(Cfg16<TX, TY, NA, NB>::kThreads, MINB)
     const int e = sc->e[sn];
     const int e_o = scale_exponent(fmaxf(__uint_as_float(sc->amax[sn]), src_hint));
     typename K::Factors fc;
-    const float cw = pow2f(112 - kW16Exp);
+    const float cw = pow2f(-kW16Exp);
     fc.c = Coeffs{a.c.c1 * cw, a.c.c2 * cw, a.c.c3 * cw, a.c.c4 * cw};
     fc.wtrue = cw;
-    fc.amp2r = scale2(1.0f, e + Fmt::kRawExp);
-    fc.ro = pow2f(e_o - e - Fmt::kRawExp);
-    fc.r2t = -e - Fmt::kRawExp;
+    fc.amp2r = scale2(1.0f, e);
+    fc.ro = pow2f(e_o - e);
+    fc.r2t = -e;
 
     if (threadIdx.x == 0) {
         if (blockIdx.x == 0) {
@@ -540,12 +700,12 @@ __global__ void __launch_bounds__(Cfg16<TX, TY, NA, NB>::kThreads, MINB)
     }
 }
 
-template <class Fmt, int TX, int TY, int NA, int NB, int MINB>
+template <class Fmt, int TX, int TY, int NA, int NB, int NU, int MINB>
 cudaError_t launch16(const Maps16 &maps, uint16_t *u_out, uint16_t *d_io, const StepArgs &a,
                      Scale16 *sc, long long step, float src_hint, int zb, const int *rec_ptr,
                      const RecEntry *rec, cudaStream_t s) {
     using Cfg = Cfg16<TX, TY, NA, NB>;
-    auto kern = step_stream16_kernel<Fmt, TX, TY, NA, NB, MINB>;
+    auto kern = step_stream16_kernel<Fmt, TX, TY, NA, NB, NU, MINB>;
     // the shared-memory limit is a per-device property of the kernel
     static LaunchFacts lf;
     int dev = 0;
@@ -570,22 +730,23 @@ cudaError_t launch16(const Maps16 &maps, uint16_t *u_out, uint16_t *d_io, const 
     return cudaGetLastError();
 }
 
-// Only 64-wide tiles: a half-warp then reads one 128-byte ring row with
-// 64-bit loads, which is conflict-free; in a 32-wide tile a half-warp would
-// read two rows whose banks overlap.
 template <class Fmt>
 cudaError_t dispatch16(const Maps16 &maps, uint16_t *u_out, uint16_t *d_io, const StepArgs &a,
                        Scale16 *sc, long long step, float src_hint, const StreamTiling &t,
                        const int *rec_ptr, const RecEntry *rec, cudaStream_t s) {
-    if (t.tx == 64 && t.ty == 8)
-        return launch16<Fmt, 64, 8, 8, 4, 3>(maps, u_out, d_io, a, sc, step, src_hint, t.zb, rec_ptr,
-                                             rec, s);
+    // planes 3 at a time (the queue rotates every 3 planes), 2 CTAs per SM
+    // at <= 168 registers: unrolling 9 planes (no rotation) ran 4-27% slower
+    // (instruction cache), a 128-register cap for 3 CTAs per SM spilled and
+    // ran at half speed, and no cap (188 registers) at 60%
+    if (t.tx == 64 && t.ty == 16)
+        return launch16<Fmt, 64, 16, 8, 4, 3, 2>(
+            maps, u_out, d_io, a, sc, step, src_hint, t.zb, rec_ptr, rec, s);
     return cudaErrorInvalidValue;
 }
 
 }  // namespace
 
-bool stream16_tiling_supported(int tx, int ty) { return tx == 64 && ty == 8; }
+bool stream16_tiling_supported(int tx, int ty) { return tx == 64 && ty == 16; }
 
 cudaError_t launch_step_stream16(int storage, const CUtensorMap *tmap_u, const CUtensorMap *tmap_d,
                                  const CUtensorMap *tmap_w, uint16_t *u_out, uint16_t *d_io,
@@ -648,8 +809,8 @@ __global__ void decode_kernel(const uint16_t *__restrict__ U, const uint16_t *__
     if (i >= g.nx) return;
     const long long p = pidx(g, i, j, k);
     const float4 v = Fmt::decode(make_uint2((unsigned)U[p] | ((unsigned)D[p] << 16), 0u));
-    const float un = scale2(v.x, -sc->e[slot] - Fmt::kRawExp);
-    const float dn = scale2(v.y, -sc->e[slot] - Fmt::kRawExp);
+    const float un = scale2(v.x, -sc->e[slot]);
+    const float dn = scale2(v.y, -sc->e[slot]);
     u[p] = un;
     up[p] = un - dn;
 }
