@@ -38,9 +38,11 @@
 // 2^12, 16x below the FP16 maximum; exponents and maxima live in a 4-slot
 // ring (Scale16) indexed by step, so no host synchronization is needed.
 //
-// Decoding is exact and cheap: BF16 is the upper half of an FP32 (one shift
-// or mask), FP16 goes through the hardware conversion (one instruction per
-// value, measured 6% faster than rebuilding the bits with integer logic). The
+// Decoding is exact and cheap: both formats go through the hardware
+// conversion, one instruction per value (for FP16 measured 6% faster than
+// rebuilding the FP32 bits with integer logic; for BF16, whose bits are the
+// upper half of an FP32, the same speed as shifts and masks but 2 registers
+// fewer, which removed a spill). The
 // kernel computes on the stored values: every input of one field carries the
 // same power-of-two factor, the model's factor 2^kW16Exp is folded into the
 // stencil weights, and the factors meet in exact power-of-two multiplies.
@@ -70,9 +72,17 @@ __device__ __forceinline__ float2 f16x2_to_f32(unsigned w) {
 }
 
 struct Bf16Fmt {
+    static __device__ __forceinline__ float2 two(unsigned w) {
+        float2 r;
+        asm("{\n\t.reg .b16 l, h;\n\tmov.b32 {l, h}, %2;\n\t"
+            "cvt.f32.bf16 %0, l;\n\tcvt.f32.bf16 %1, h;\n\t}"
+            : "=f"(r.x), "=f"(r.y)
+            : "r"(w));
+        return r;
+    }
     static __device__ __forceinline__ float4 decode(uint2 v) {
-        return make_float4(__uint_as_float(v.x << 16), __uint_as_float(v.x & 0xffff0000u),
-                           __uint_as_float(v.y << 16), __uint_as_float(v.y & 0xffff0000u));
+        const float2 a = two(v.x), b = two(v.y);
+        return make_float4(a.x, a.y, b.x, b.y);
     }
     static __device__ __forceinline__ uint2 encode(float4 f) {
         uint2 r;
@@ -116,14 +126,13 @@ struct Cfg16 {
     // four corner blocks are never read by the star stencil and stay unset)
     static constexpr int kSW = TX + 2 * kHalo;
     static constexpr int kStage = kSW * kRows;
-    // halo units decoded per plane: TX units of 8 cells in the 8 bands above
-    // and below the tile (threads 0..TX-1), 2*TY units of 4 cells beside it
-    // (threads kSide0..), whole warps of one kind
-    static constexpr int kBandUnits = TX;
-    static constexpr int kSide0 = (kBandUnits + 31) / 32 * 32;
+    // halo cells decoded per plane, in units of 4 cells: 2*TX units in the 8
+    // rows above and below the tile (one per consumer thread), 2*TY = 32
+    // units beside it (the last consumer warp, one per lane)
+    static constexpr int kSideWarp = kConsumers / 32 - 1;
     static_assert(kConsumers % 32 == 0, "whole consumer warps");
-    static_assert(TX % 64 == 0 && TY % 2 == 0, "64-wide tiles, row pairs");
-    static_assert(kSide0 + 2 * TY <= kConsumers, "one halo unit per consumer thread at most");
+    static_assert(TX % 64 == 0 && TY == 16, "64-wide tiles of 16 rows (8 row pairs)");
+    static_assert(2 * TX == kConsumers && 2 * TY == 32, "one band unit per thread, one side warp");
     static_assert((NA & (NA - 1)) == 0 && NA >= 8 && (NB & (NB - 1)) == 0 && NB >= 2, "rings");
     static_assert(kSlotABytes % 128 == 0 && kSlotBBytes % 128 == 0 && (kStage * 4) % 128 == 0,
                   "slots stay 128-byte aligned");
@@ -227,6 +236,7 @@ struct Walk16 {
     uint16_t *out_k;    // U' of (i, j, k); D of it at out_k + d_delta, row j+1 one pitch on
     int nvalid;         // valid x cells of the rows (0: none)
     bool row1;          // row j+1 inside the grid
+    bool full;          // all 8 cells inside the grid
     int rcur, rend, rnext_k;
     unsigned src_mask;
     unsigned gAw, gAr, gB;
@@ -234,10 +244,11 @@ struct Walk16 {
     bool ok;
 };
 
-// A thread's halo unit: ring-A element offset, staging offset, kind (0 none,
-// 1 eight cells of a band row, 2 four cells beside the tile).
+// A thread's halo units: ring-A element offset and staging offset of its 4
+// cells above or below the tile, and (last consumer warp) of its 4 cells
+// beside the tile.
 struct Halo {
-    int src, dst, kind;
+    int band_src, band_dst, side_src, side_dst;
 };
 
 template <class Fmt, int TX, int TY, int NA, int NB, int NU>
@@ -310,20 +321,18 @@ struct Kern16 {
         }
     }
 
-    static __device__ __forceinline__ Halo halo_unit(int tid) {
-        Halo h{0, 0, 0};
-        if (tid < Cfg::kBandUnits) {
-            const int per_row = TX / 8;
-            const int band = tid / per_row, n = tid - band * per_row;
-            const int y = band < kHalo ? band : TY + band;      // rows 0..3, TY+4..TY+7
-            const int c = kHalo + 8 * n;                          // staging column
-            h = Halo{y * Cfg::kRowW + c + (Cfg::kLead - kHalo), y * Cfg::kSW + c, 1};
-        } else if (tid >= Cfg::kSide0 && tid < Cfg::kSide0 + 2 * TY) {
-            const int v = tid - Cfg::kSide0;
-            const int y = kHalo + (v >> 1);
-            const int c = (v & 1) ? TX + kHalo : 0;
-            h = Halo{y * Cfg::kRowW + c + (Cfg::kLead - kHalo), y * Cfg::kSW + c, 2};
-        }
+    static __device__ __forceinline__ Halo halo_units(int tid) {
+        Halo h;
+        const int band = tid / Cfg::kCols, n = tid - band * Cfg::kCols;
+        int y = band < kHalo ? band : TY + band;            // rows 0..3, TY+4..TY+7
+        int c = kHalo + 4 * n;                                // staging column
+        h.band_src = y * Cfg::kRowW + c + (Cfg::kLead - kHalo);
+        h.band_dst = y * Cfg::kSW + c;
+        const int v = tid & 31;
+        y = kHalo + (v >> 1);
+        c = (v & 1) ? TX + kHalo : 0;
+        h.side_src = y * Cfg::kRowW + c + (Cfg::kLead - kHalo);
+        h.side_dst = y * Cfg::kSW + c;
         return h;
     }
 
@@ -412,14 +421,10 @@ struct Kern16 {
         sts4(st + offS, wk.q[Q4][0]);
         sts4(st + offS + Cfg::kSW, wk.q[Q4][1]);
         {
-            const uint16_t *src = ringA + (wk.gAr & (NA - 1)) * Cfg::kSlotA + hu.src;
-            if (hu.kind == 1) {
-                const uint4 v = lds4u(src);
-                sts4(st + hu.dst, Fmt::decode(make_uint2(v.x, v.y)));
-                sts4(st + hu.dst + 4, Fmt::decode(make_uint2(v.z, v.w)));
-            } else if (hu.kind == 2) {
-                sts4(st + hu.dst, Fmt::decode(lds2u(src)));
-            }
+            const uint16_t *src = ringA + (wk.gAr & (NA - 1)) * Cfg::kSlotA;
+            sts4(st + hu.band_dst, Fmt::decode(lds2u(src + hu.band_src)));
+            if ((threadIdx.x >> 5) == Cfg::kSideWarp)
+                sts4(st + hu.side_dst, Fmt::decode(lds2u(src + hu.side_src)));
         }
         wk.ok = consumers_all(wk.ok, Cfg::kConsumers);
         warp_arrive(&rg.emptyA[wk.gAr & (NA - 1)]);
@@ -467,21 +472,30 @@ struct Kern16 {
                                              fmaxf(fabsf(un[0].z), fabsf(un[0].w))),
                                        fmaxf(fmaxf(fabsf(un[1].x), fabsf(un[1].y)),
                                              fmaxf(fabsf(un[1].z), fabsf(un[1].w)))));
-        if (wk.nvalid > 0) {
+        // increments u~ - u, then the stored values of both rows
+        uint2 su[2], sd[2];
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const float4 xc = wk.q[Q4][r];
+            const float2 d0 = add2(lo2(un[r]), make_float2(-xc.x, -xc.y));
+            const float2 d1 = add2(hi2(un[r]), make_float2(-xc.z, -xc.w));
+            const float2 u0 = mul2(lo2(un[r]), splat(fc.ro)), u1 = mul2(hi2(un[r]), splat(fc.ro));
+            const float2 e0 = mul2(d0, splat(fc.ro)), e1 = mul2(d1, splat(fc.ro));
+            su[r] = Fmt::encode(make_float4(u0.x, u0.y, u1.x, u1.y));
+            sd[r] = Fmt::encode(make_float4(e0.x, e0.y, e1.x, e1.y));
+        }
+        if (wk.full) {
 #pragma unroll
             for (int r = 0; r < 2; ++r) {
-                if (r == 1 && !wk.row1) break;
-                const float4 xc = wk.q[Q4][r];
-                // increments u~ - u, then the stored values
-                const float2 d0 = add2(lo2(un[r]), make_float2(-xc.x, -xc.y));
-                const float2 d1 = add2(hi2(un[r]), make_float2(-xc.z, -xc.w));
-                const float2 su0 = mul2(lo2(un[r]), splat(fc.ro));
-                const float2 su1 = mul2(hi2(un[r]), splat(fc.ro));
-                const float2 sd0 = mul2(d0, splat(fc.ro)), sd1 = mul2(d1, splat(fc.ro));
-                uint16_t *o = wk.out_k + r * a.g.pnx;
-                store16(o, Fmt::encode(make_float4(su0.x, su0.y, su1.x, su1.y)), wk.nvalid);
-                store16(o + d_delta, Fmt::encode(make_float4(sd0.x, sd0.y, sd1.x, sd1.y)),
-                        wk.nvalid);
+                store16(wk.out_k + r * a.g.pnx, su[r], 4);
+                store16(wk.out_k + r * a.g.pnx + d_delta, sd[r], 4);
+            }
+        } else if (wk.nvalid > 0) {
+            store16(wk.out_k, su[0], wk.nvalid);
+            store16(wk.out_k + d_delta, sd[0], wk.nvalid);
+            if (wk.row1) {
+                store16(wk.out_k + a.g.pnx, su[1], wk.nvalid);
+                store16(wk.out_k + a.g.pnx + d_delta, sd[1], wk.nvalid);
             }
         }
         wk.out_k += a.g.plane;
@@ -505,11 +519,10 @@ struct Kern16 {
                                                   const Item &it, int kb, int i, int j, int offA,
                                                   int offB, int offS, const RecEntry *rec) {
         if constexpr (RQ < NU) {
-            if (kb + RQ >= it.z1) return false;
+            // wk.ok is the same in every consumer after a staging barrier
+            if (kb + RQ >= it.z1 || !wk.ok) return false;
             plane_step<RQ>(wk, rg, ringA, ringB, stage, a, fc, d_delta, hu, kb + RQ, i, j, offA,
                            offB, offS, rec);
-            // wk.ok is the same in every consumer after the staging barrier
-            if (!wk.ok) return false;
             return planes<RQ + 1>(wk, rg, ringA, ringB, stage, a, fc, d_delta, hu, it, kb, i, j,
                                   offA, offB, offS, rec);
         }
@@ -551,7 +564,7 @@ struct Kern16 {
         const int offA = (kHalo + 2 * py) * Cfg::kRowW + Cfg::kLead + 4 * tx;
         const int offB = 2 * py * TX + 4 * tx;
         const int offS = (kHalo + 2 * py) * Cfg::kSW + kHalo + 4 * tx;
-        const Halo hu = halo_unit(tid);
+        const Halo hu = halo_units(tid);
         Walk16 wk;
         wk.gAw = wk.gAr = wk.gB = 0;
         wk.ok = true;
@@ -563,6 +576,7 @@ struct Kern16 {
             const bool col_ok = (j < g.ny) && (i < g.nx);
             wk.nvalid = col_ok ? min(4, g.nx - i) : 0;
             wk.row1 = j + 1 < g.ny;
+            wk.full = wk.nvalid == 4 && wk.row1;
 #pragma unroll
             for (int r = 0; r < 2; ++r) {
                 wk.gxy[r] = make_float4(0.f, 0.f, 0.f, 0.f);
