@@ -656,6 +656,8 @@ def main():
     wsb.ws_destroy(h)
     if world == 1 and not args.no_storage16 and n >= 64:
         line["storage16"] = storage16_report(w, K, W, stream, peak)
+        for mode in line["storage16"].values():     # speed relative to FP32 storage
+            mode["vs_fp32_storage"] = mode["value"] / line["value"]
     if world == 1 and not args.no_batched:
         line["batched"] = batched_report(peak)
     if world == 1 and not args.no_adjoint:
