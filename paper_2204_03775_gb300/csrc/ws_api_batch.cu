@@ -173,8 +173,10 @@ void batch_free(ws_batch_t b) {
 }
 
 // Configure every shot for tile tx x ty with z-blocks for m x slots items
-// (m = 0: each shot's default) and rebuild the item table: shots in order
-// of decreasing size, each shot's items block-major.
+// (m = 0: each shot's default) and rebuild the item table: longest items
+// (most planes) first, so the last wave of the launch holds the shortest
+// ones; among equal lengths, shots in order of decreasing size and each
+// shot's items block-major (neighbouring tiles run together).
 int batch_configure(ws_batch_t b, int tx, int ty, int m) {
     int slots = 0;
     WS_CUDA(ws::stream_slots(tx, ty, true, &slots), "ws_batch_step");
@@ -188,6 +190,7 @@ int batch_configure(ws_batch_t b, int tx, int ty, int m) {
         return (long long)gx.nx * gx.ny * gx.nz > (long long)gy.nx * gy.ny * gy.nz;
     });
     std::vector<int2> items;
+    std::vector<int> planes;   // z extent of each item
     b->zb.assign(n, 0);
     for (int q : order) {
         ws_t ws = b->shots[q];
@@ -210,8 +213,17 @@ int batch_configure(ws_batch_t b, int tx, int ty, int m) {
         int rc = build_rec_tiles(ws, ws::StreamTiling{tx, ty, zb});
         if (rc != WS_OK) return rc;
         const long long nit = tiles * ((g.nz + zb - 1) / zb);
-        for (long long l = 0; l < nit; ++l) items.push_back(make_int2(q, (int)l));
+        for (long long l = 0; l < nit; ++l) {
+            items.push_back(make_int2(q, (int)l));
+            planes.push_back((int)std::min<long long>(zb, g.nz - (l / tiles) * zb));
+        }
     }
+    std::vector<int> perm(items.size());
+    for (size_t x = 0; x < perm.size(); ++x) perm[x] = (int)x;
+    std::stable_sort(perm.begin(), perm.end(), [&](int x, int y) { return planes[x] > planes[y]; });
+    std::vector<int2> sorted(items.size());
+    for (size_t x = 0; x < perm.size(); ++x) sorted[x] = items[perm[x]];
+    items.swap(sorted);
     if ((long long)items.size() > INT32_MAX / 2)
         return fail(WS_ERR_BADARG, "ws_batch_step: too many work items");
     batch_drop_graphs(b);
