@@ -249,7 +249,7 @@ int ws_forward(ws_t ws);
  * tile and needs nx >= 64, ny >= 16, else BADARG. ws_read_field, ws_write_field
  * and ws_energy convert to and from FP32 (ws_energy then uses the FP32
  * model). Relative L2 error against FP32 storage on the 1024^3 layered
- * survey, measured: FP16 8.6e-4, 3.0e-3, 4.3e-3 after 100, 500, 1000 steps;
+ * survey, measured: FP16 7.9e-4, 2.9e-3, 4.2e-3 after 100, 500, 1000 steps;
  * BF16 6.2e-3, 2.4e-2, 3.8e-2. This realizes the reduced-precision storage
  * that the paper contrasts with its FP32-only arithmetic (Section I). */
 int ws_set_storage(ws_t ws, int storage);
