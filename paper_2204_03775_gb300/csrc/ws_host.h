@@ -154,7 +154,8 @@ int build_rec_tiles(ws_t ws, const ws::StreamTiling &t, int rows = 1);
 int copy_in(ws_t ws, float *dst, const float *src, int on_device);
 int copy_out(ws_t ws, float *dst, const float *src, int on_device);
 int upload_profiles(ws_t ws);
-// The tile of the 16-bit streaming kernel.
+// The tile of the 16-bit streaming kernel and the rows each of its consumer
+// threads computes.
 constexpr int kTile16X = 64, kTile16Y = 16, kRows16 = 2;
 int encode_maps16(ws_t ws);
 int encode_state16(ws_t ws);
