@@ -326,8 +326,9 @@ long long ws_batch_launch_count(ws_batch_t b);
 int ws_synchronize(ws_t ws);
 
 /* Test hook for the failure path (the paper has no counterpart): the next
- * ws_step that uses the streaming FP32 kernel withholds the first copy of
- * work item `item` (items are numbered z block by z block, then by tile),
+ * ws_step that uses a streaming kernel (FP32, or the 16-bit kernel of
+ * 16-bit storage) withholds the first copy of work item `item` (items are
+ * numbered z block by z block, then by tile),
  * so the bounded waits of the CTA that owns it give up after about one
  * second. That step's result is then invalid: ws_synchronize returns
  * TIMEOUT, and the caller must write a new state (ws_write_field) before

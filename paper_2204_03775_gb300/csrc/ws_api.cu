@@ -664,10 +664,13 @@ int ws_step(ws_t ws, int nsteps) {
             double hint = 0.0;
             for (int q = 0; q < a.src.n; ++q)
                 hint = std::max(hint, std::fabs((double)a.src.s[q].amp) * ws->wmax);
+            a.stall_item = ws->stall_item;
+            ws->stall_item = -1;
             cudaError_t e = ws::launch_step_stream16(
                 ws->storage, &ws->t16_halo[ws->cur], &ws->t16_d, &ws->t16_w,
                 ws->buf16[1 - ws->cur], ws->d16, a, ws->scale, ws->step, (float)hint, tiling,
                 ws->nrec > 0 ? ws->rec_ptr : nullptr, ws->rec_entries, ws->stream);
+            a.stall_item = -1;
             ws->launches++;
             if (e != cudaSuccess) return cuda_fail(e, "ws_step launch");
         } else {

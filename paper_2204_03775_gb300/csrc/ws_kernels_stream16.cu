@@ -352,8 +352,13 @@ struct Kern16 {
         for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
             const Item it = item_of(item, tiles_x, ntiles, zb, a.g.nz, TX, TY);
             const int nb = it.z1 - it.z0, nplanes = nb + 2 * kHalo;
-            for (int pr = 0; pr < 2 * kHalo; ++pr)
+            for (int pr = 0; pr < 2 * kHalo; ++pr) {
+                if (pr == 0 && item == a.stall_item) {   // test hook: never filled, so the
+                    ++gA;                                 // consumers' bounded waits run out
+                    continue;
+                }
                 if (!produce_a(rg, ringA, mp, gA++, it, pr, a.status)) return;
+            }
             for (int b = 0; b < nb; ++b) {
                 if (!produce_b(rg, ringB, mp, gB++, it, b, a.status)) return;
                 if (b + 2 * kHalo < nplanes &&

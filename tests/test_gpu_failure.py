@@ -6,6 +6,9 @@ timeout in the handle's status word, every warp of that CTA leaves its
 loops, the CTA drains its own copies in flight, and the launch ends.
 ws_synchronize must report WS_ERR_TIMEOUT once, the CUDA context must stay
 usable, and after a fresh state the handle must step exactly as a new one.
+Both streaming kernels: the FP32 one (warps leave together by a warp vote)
+and the 16-bit one (its consumer warps meet at a named barrier every plane,
+which also ANDs their wait flags, so all of them leave at the same plane).
 """
 
 import time
@@ -19,8 +22,9 @@ from paper_2204_03775_gb300 import synthetic
 pytestmark = pytest.mark.gpu
 
 
-def _handle(w):
+def _handle(w, storage=wsb.WS_STORAGE_FP32):
     h = wsb.ws_create(w.nx, w.ny, w.nz, w.h, w.dt)
+    wsb.ws_set_storage(h, storage)
     wsb.ws_set_velocity(h, w.vel)
     wsb.ws_set_sponge(h, *w.sponge)
     for s in w.sources:
@@ -29,10 +33,11 @@ def _handle(w):
     return h
 
 
-def test_bounded_wait_timeout_is_reported_and_recoverable():
+@pytest.mark.parametrize("storage", [wsb.WS_STORAGE_FP32, wsb.WS_STORAGE_FP16])
+def test_bounded_wait_timeout_is_reported_and_recoverable(storage):
     wsb.load_library(build_if_missing=True)
     w = synthetic.layered_survey(128, 64, 48, nt=20)
-    h = _handle(w)
+    h = _handle(w, storage)
     wsb.ws_step(h, 3)
     wsb.ws_synchronize(h)
     wsb.ws_test_stall(h, 5)
@@ -48,7 +53,7 @@ def test_bounded_wait_timeout_is_reported_and_recoverable():
     wsb.ws_write_field(h, None, None, 0)
     wsb.ws_step(h, 20)
     wsb.ws_synchronize(h)
-    ref = _handle(w)
+    ref = _handle(w, storage)
     wsb.ws_step(ref, 20)
     u, up = wsb.ws_read_field(h)
     ur, upr = wsb.ws_read_field(ref)
