@@ -327,11 +327,13 @@ int ws_synchronize(ws_t ws);
 
 /* Test hook for the failure path (the paper has no counterpart): the next
  * ws_step that uses a streaming kernel (FP32, or the 16-bit kernel of
- * 16-bit storage) withholds the first copy of work item `item` (items are
- * numbered z block by z block, then by tile),
+ * 16-bit storage), or the first step of the next ws_batch_step run that
+ * includes this shot, withholds the first copy of the shot's work item
+ * `item` (items are numbered z block by z block, then by tile),
  * so the bounded waits of the CTA that owns it give up after about one
- * second. That step's result is then invalid: ws_synchronize returns
- * TIMEOUT, and the caller must write a new state (ws_write_field) before
+ * second. That step's result is then invalid: ws_synchronize (for a batch,
+ * ws_batch_synchronize) returns TIMEOUT, and the caller must write a new
+ * state (ws_write_field) before
  * stepping on; the handle and the CUDA context stay usable. item = -1
  * clears a pending stall. No GPU fault is involved: the kernel only stops
  * waiting, records the status and drains its own copies. */

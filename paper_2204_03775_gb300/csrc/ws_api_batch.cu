@@ -302,6 +302,8 @@ int batch_upload(ws_batch_t b, int nsteps) {
         x.zb = b->zb[q];
         x.tiles_x = (ws->g.nx + b->tx - 1) / b->tx;
         x.ntiles = x.tiles_x * ((ws->g.ny + b->ty - 1) / b->ty);
+        x.stall_item = ws->stall_item;   // test hook, for the first step of this run only
+        ws->stall_item = -1;
     }
     if (!b->d_shots)
         WS_CUDA(cudaMalloc(&b->d_shots, sizeof(ws::BatchShot) * n), "cudaMalloc batch shots");

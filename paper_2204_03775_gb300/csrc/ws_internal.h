@@ -127,6 +127,8 @@ cudaError_t launch_step_stream(const CUtensorMap *tmap_u, const CUtensorMap *tma
 // halo[cur0 ^ (t & 1)], u^{n-1} with tile[the other], writes u^{n+1} over
 // u^{n-1}; src holds nsrc samples per step of the run ([t][nsrc]); trace
 // column of step t = trace_col0 + t (traces null: no receivers).
+// stall_item (test hook): the first step of the run withholds the first
+// copy of this shot's work item stall_item (-1: none).
 struct alignas(128) BatchShot {
     CUtensorMap halo[2], tile[2], w;
     float *buf[2];
@@ -137,7 +139,7 @@ struct alignas(128) BatchShot {
     const RecEntry *rec;
     Geom g;
     long long trace_col0;
-    int nsrc, nt_max, cur0, zb, tiles_x, ntiles;
+    int nsrc, nt_max, cur0, zb, tiles_x, ntiles, stall_item;
 };
 
 // SMs x resident CTAs of the streaming kernel (batch: the batched one) with

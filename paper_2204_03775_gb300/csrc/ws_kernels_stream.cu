@@ -154,7 +154,7 @@ struct ShotBatch {
         const BatchShot &s = shots[e.x];
         const int p = s.cur0 ^ (t & 1);
         return Job{item_of(e.y, s.tiles_x, s.ntiles, s.zb, s.g.nz, TX, TY), &s.halo[p],
-                   &s.tile[1 - p], &s.w, false};
+                   &s.tile[1 - p], &s.w, t == 0 && e.y == s.stall_item};
     }
     __device__ __forceinline__ Item view(int item, View *v) const {
         const int2 e = items[item];

@@ -6,9 +6,10 @@ timeout in the handle's status word, every warp of that CTA leaves its
 loops, the CTA drains its own copies in flight, and the launch ends.
 ws_synchronize must report WS_ERR_TIMEOUT once, the CUDA context must stay
 usable, and after a fresh state the handle must step exactly as a new one.
-Both streaming kernels: the FP32 one (warps leave together by a warp vote)
-and the 16-bit one (its consumer warps meet at a named barrier every plane,
-which also ANDs their wait flags, so all of them leave at the same plane).
+All three streaming kernels: the FP32 one (warps leave together by a warp
+vote), the 16-bit one (its consumer warps meet at a named barrier every
+plane, which also ANDs their wait flags, so all of them leave at the same
+plane) and the batched one (the FP32 body over a table of shots).
 """
 
 import time
@@ -60,6 +61,38 @@ def test_bounded_wait_timeout_is_reported_and_recoverable(storage):
     np.testing.assert_array_equal(u, ur)
     np.testing.assert_array_equal(up, upr)
     assert np.abs(u).max() > 0
+
+
+def test_batch_stall_is_reported_and_recoverable():
+    """The same hook in a batch: the first launch of the run withholds one
+    copy of one shot's item; the batch reports the timeout once, and after
+    fresh states every shot steps exactly like a shot stepped alone."""
+    wsb.load_library(build_if_missing=True)
+    ws = [synthetic.layered_survey(128, 64, 48, nt=20), synthetic.layered_survey(96, 40, 30, nt=20)]
+    hs = [_handle(w) for w in ws]
+    b = wsb.ws_batch_create(hs)
+    wsb.ws_batch_set_tiling(b, 32, 16, 0)
+    wsb.ws_batch_step(b, 2)
+    wsb.ws_batch_synchronize(b)
+    wsb.ws_test_stall(hs[1], 3)
+    t0 = time.perf_counter()
+    wsb.ws_batch_step(b, 3)
+    with pytest.raises(wsb.WaveStepError) as e:
+        wsb.ws_batch_synchronize(b)
+    took = time.perf_counter() - t0
+    assert e.value.code == wsb.WS_ERR_TIMEOUT
+    assert 0.5 < took < 30.0, took
+    wsb.ws_batch_synchronize(b)                 # reported once, then cleared
+    for h in hs:
+        wsb.ws_write_field(h, None, None, 0)
+    wsb.ws_batch_step(b, 20)
+    wsb.ws_batch_synchronize(b)
+    for h, w in zip(hs, ws):
+        ref = _handle(w)
+        wsb.ws_step(ref, 20)
+        np.testing.assert_array_equal(wsb.ws_read_field(h)[0], wsb.ws_read_field(ref)[0])
+        np.testing.assert_array_equal(wsb.ws_read_field(h)[1], wsb.ws_read_field(ref)[1])
+    wsb.ws_batch_destroy(b)
 
 
 def test_stall_hook_arguments():
