@@ -2,8 +2,7 @@
 //
 // Same pipeline as the FP32 streaming kernel (one CTA per work item in item
 // order, one TMA producer lane, 9-plane register queue, fused
-// taper/source/receivers), but
-// the state is stored as
+// taper/source/receivers), but the state is stored as
 //     U = u^n   and   D = u^n - u^{n-1}   (16 bits each),
 // and the model as FP16 of (V dt/h)^2 * 2^kW16Exp: 10 bytes per cell update
 // (read U, D, W; write U', D'). All arithmetic is FP32; the step computes
@@ -25,8 +24,9 @@
 // decoded once: a thread decodes its own cells of plane k+4 into its register
 // queue, and at plane k writes them (FP32) into a double-buffered staging
 // tile; the cells around the tile that the star stencil reads (not the
-// corners) are decoded into the same tile by one unit of work per thread.
-// The consumer warps then agree at a named barrier that also ANDs their "no
+// corners) are decoded into the same tile, 4 cells per consumer thread above
+// and below the tile and 4 per lane of the last warp beside it. The consumer
+// warps then agree at a named barrier that also ANDs their "no
 // wait failed" flags (so a bounded wait that gives up stops every consumer
 // warp at the same plane) and read their x/y neighbours from the staging tile
 // with 128-bit loads. Each thread computes 4 x-cells of two rows.
@@ -42,11 +42,11 @@
 // conversion, one instruction per value (for FP16 measured 6% faster than
 // rebuilding the FP32 bits with integer logic; for BF16, whose bits are the
 // upper half of an FP32, the same speed as shifts and masks but 2 registers
-// fewer, which removed a spill). The
-// kernel computes on the stored values: every input of one field carries the
-// same power-of-two factor, the model's factor 2^kW16Exp is folded into the
-// stencil weights, and the factors meet in exact power-of-two multiplies.
-// Results are rounded to 16 bits once, when stored.
+// fewer, which removed a spill). The kernel computes on the stored values:
+// every input of one field carries the same power-of-two factor, the model's
+// factor 2^kW16Exp is folded into the stencil weights, and the factors meet
+// in exact power-of-two multiplies. Results are rounded to 16 bits once,
+// when stored.
 #include <climits>
 
 #include "ws_ptx.cuh"
@@ -140,14 +140,7 @@ struct Cfg16 {
         size_t(2 * kStage) * 4u + size_t(NA) * kSlotABytes + size_t(NB) * kSlotBBytes;
 };
 
-// 128-bit shared loads and stores.
-__device__ __forceinline__ uint4 lds4u(const uint16_t *p) {
-    uint4 v;
-    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
-                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
-                 : "r"(smem_addr(p)));
-    return v;
-}
+// 128-bit shared store.
 __device__ __forceinline__ void sts4(float *p, float4 v) {
     asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(smem_addr(p)), "f"(v.x),
                  "f"(v.y), "f"(v.z), "f"(v.w)
@@ -368,15 +361,10 @@ struct Kern16 {
         }
     }
 
-    static __device__ __forceinline__ void store16(uint16_t *p, const uint2 st, int nvalid) {
-        if (nvalid == 4) {
-            asm volatile("st.global.cs.v2.u32 [%0], {%1, %2};" ::"l"(p), "r"(st.x), "r"(st.y)
-                         : "memory");
-        } else {
-            p[0] = (uint16_t)(st.x & 0xffffu);
-            if (nvalid > 1) p[1] = (uint16_t)(st.x >> 16);
-            if (nvalid > 2) p[2] = (uint16_t)(st.y & 0xffffu);
-        }
+    // 4 stored values (8 bytes), streaming store.
+    static __device__ __forceinline__ void store16(uint16_t *p, const uint2 st) {
+        asm volatile("st.global.cs.v2.u32 [%0], {%1, %2};" ::"l"(p), "r"(st.x), "r"(st.y)
+                     : "memory");
     }
 
     static __device__ __forceinline__ Halo halo_units(int tid) {
@@ -535,8 +523,8 @@ struct Kern16 {
         if (wk.full) {
 #pragma unroll
             for (int r = 0; r < 2; ++r) {
-                store16(wk.out_k + r * a.g.pnx, su[r], 4);
-                store16(wk.out_k + r * a.g.pnx + d_delta, sd[r], 4);
+                store16(wk.out_k + r * a.g.pnx, su[r]);
+                store16(wk.out_k + r * a.g.pnx + d_delta, sd[r]);
             }
         } else if (wk.nvalid > 0) {
             store_partial(wk.out_k, d_delta, a.g.pnx, su[0], sd[0], su[1], sd[1], wk.nvalid,
