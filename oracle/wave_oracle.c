@@ -137,7 +137,7 @@ double or_cerjan(int idx, int n, int nb, double a)
 }
 
 /* Ricker wavelet amp (1 - 2 pi^2 f0^2 tau^2) exp(-pi^2 f0^2 tau^2), tau = t - t0:
- * the source time function f^n of Eq. 2 used by this build. */
+ * the source time function f^n of Eq. 2 as used here (the paper names none). */
 double or_ricker(double t, double f0, double t0, double amp)
 {
     const double pi = 3.14159265358979323846;

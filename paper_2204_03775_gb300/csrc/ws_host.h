@@ -47,7 +47,7 @@ struct SourceDef {
     double f0, t0, amp;
 };
 
-// The driver's cuTensorMapEncodeTiled (null when unavailable).
+// The CUDA driver API's cuTensorMapEncodeTiled (null when unavailable).
 PFN_cuTensorMapEncodeTiled_v12000 get_encode_fn();
 
 }  // namespace wsh
