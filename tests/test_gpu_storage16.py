@@ -9,7 +9,9 @@ model (V dt/h)^2 in FP16.
    computes the same FP32 operations on exactly power-of-two-scaled numbers.
 2. Accuracy against the FP64 oracle over many steps, checked against the
    bounds stated in the header and the design notes (the rounding of U' each
-   step dominates; FP32 storage stays near 1e-6).
+   step dominates; FP32 storage stays near 1e-6), and at the benchmark's full
+   size (1024^3, 100 steps) against FP32 storage and against the oracle on
+   the light cone.
 3. Converting FP32 -> 16-bit -> FP32 keeps the state within one 16-bit rounding.
 """
 
@@ -151,12 +153,13 @@ def test_storage_needs_a_64_wide_grid():
     assert e.value.code == wsb.WS_ERR_BADARG
 
 
-def test_full_size_accuracy_against_fp32():
+def test_full_size_accuracy_against_fp32_and_oracle():
     """The benchmark's 1024^3 survey, 100 steps: each 16-bit mode against FP32
-    storage (itself within 3e-6 of the FP64 oracle there), on the device,
-    in the launch configurations bench.py times (the 16-bit kernel's 64 x 16
-    tile, the FP32 kernel's default 64 x 8, default z blocks). Bounds from the
-    measured 7.9e-4 (FP16) and 6.2e-3 (BF16)."""
+    storage on the device, and every mode against the FP64 oracle on the
+    light cone, in the launch configurations bench.py times (the 16-bit
+    kernel's 64 x 16 tile, the FP32 kernel's default 64 x 8, default z
+    blocks). Bounds from the measured 7.9e-4 (FP16) and 6.2e-3 (BF16)
+    against FP32 storage."""
     import torch
     w = synthetic.layered_survey(1024, 1024, 1024, nt=100)
     bound = {"fp32": 0.0, "fp16": 2e-3, "bf16": 1.2e-2}
@@ -182,3 +185,25 @@ def test_full_size_accuracy_against_fp32():
         err = torch.linalg.vector_norm(out[name].double() - ref).item() / nref
         print(f"{name}: 1024^3, 100 steps, relative L2 vs FP32 storage {err:.3e}")
         assert err <= bound[name], (name, err)
+
+    # and against the FP64 oracle itself: after nt steps from rest the field
+    # is exactly zero farther than 4 nt cells from the source, so the oracle
+    # steps only the window that holds the light cone (803 x 803 x 422 cells)
+    si, sj, sk = w.sources[0][:3]
+    r = 4 * w.nt + 1
+    ox, oy, wx, wy, wz = si - r, sj - r, 2 * r + 1, 2 * r + 1, sk + r + 1
+    sub = np.ascontiguousarray(w.vel[:wz, oy:oy + wy, ox:ox + wx])
+    orc = oracle.run(sub, w.h, w.dt, w.nt, sources=w.sources, sponge=w.sponge,
+                     window=(ox, oy, 0, w.nx, w.ny, w.nz))["u"]
+    norc = np.linalg.norm(orc)
+    vs_oracle = {"fp32": 1e-4, "fp16": 2e-3, "bf16": 1.2e-2}
+    for name, bnd in vs_oracle.items():
+        u = out[name]
+        win = u[:wz, oy:oy + wy, ox:ox + wx].cpu().numpy().astype(np.float64)
+        err = np.linalg.norm(win - orc) / norc
+        print(f"{name}: 1024^3, 100 steps, relative L2 vs the FP64 oracle {err:.3e}")
+        assert err <= bnd, (name, err)
+        beyond = u.clone()                        # exactly zero beyond the light cone
+        beyond[:wz, oy:oy + wy, ox:ox + wx] = 0
+        assert torch.count_nonzero(beyond).item() == 0, name
+        del beyond
