@@ -248,10 +248,10 @@ int ws_forward(ws_t ws);
  * (rounded once). 16-bit storage runs its own streaming kernel with a 64x16
  * tile and needs nx >= 64, ny >= 16, else BADARG. ws_read_field, ws_write_field
  * and ws_energy convert to and from FP32 (ws_energy then uses the FP32
- * model). Relative L2 error on the 1024^3 layered survey, measured: against
- * the FP64 oracle after 100 steps FP16 7.9e-4, BF16 6.2e-3 (FP32 4.5e-7);
- * against FP32 storage FP16 7.9e-4, 2.9e-3, 4.2e-3 after 100, 500, 1000
- * steps, BF16 6.2e-3, 2.4e-2, 3.8e-2. This realizes the reduced-precision storage
+ * model). Relative L2 error against the FP64 oracle, measured on the layered
+ * survey at 256^3 after 100, 500, 1000 steps: FP16 8.6e-4, 2.8e-3, 5.4e-3;
+ * BF16 6.6e-3, 2.3e-2, 4.4e-2 (FP32 storage 5.7e-7 ... 2.5e-6); at 1024^3
+ * after 100 steps FP16 7.9e-4, BF16 6.2e-3. This realizes the reduced-precision storage
  * that the paper contrasts with its FP32-only arithmetic (Section I). */
 int ws_set_storage(ws_t ws, int storage);
 

@@ -125,6 +125,39 @@ def test_accuracy_against_oracle(storage, name):
     assert err <= BOUNDS[name], err
 
 
+def test_storage_modes_against_oracle_to_1000_steps():
+    """The layered survey recipe at 256^3 for the configured 1000 steps: each
+    storage mode against the FP64 oracle at steps 100, 500 and 1000 (the
+    oracle continues its own state between checkpoints). FP32 within 1e-4,
+    FP16 within 1e-2 at every checkpoint; BF16 within 6e-2 (its 8-bit
+    significand rounds the displacement by ~2e-3 per step)."""
+    w = synthetic.layered_survey(256, 256, 256, nt=1000)
+    checkpoints = (100, 500, 1000)
+    hs = {}
+    for storage, name in [(wsb.WS_STORAGE_FP32, "fp32")] + MODES:
+        hd = wsb.ws_create(w.nx, w.ny, w.nz, w.h, w.dt)
+        wsb.ws_set_storage(hd, storage)
+        wsb.ws_set_velocity(hd, w.vel)
+        wsb.ws_set_sponge(hd, *w.sponge)
+        for s in w.sources:
+            wsb.ws_add_source(hd, *s)
+        hs[name] = hd
+    bound = {"fp32": 1e-4, "fp16": 1e-2, "bf16": 6e-2}
+    v64 = w.vel.astype(np.float64)
+    ref, done = None, 0
+    for c in checkpoints:
+        kw = {} if ref is None else {"n0": done, "u_init": ref["u"], "uprev_init": ref["u_prev"]}
+        ref = oracle.run(v64, w.h, w.dt, c - done, sources=w.sources, sponge=w.sponge, **kw)
+        nref = np.linalg.norm(ref["u"])
+        for name, hd in hs.items():
+            wsb.ws_step(hd, c - done)
+            u, _ = wsb.ws_read_field(hd)
+            err = np.linalg.norm(u - ref["u"]) / nref
+            print(f"{name}: 256^3, {c} steps, relative L2 vs the FP64 oracle {err:.3e}")
+            assert err <= bound[name], (name, c, err)
+        done = c
+
+
 @pytest.mark.parametrize("storage,name", MODES)
 def test_storage_round_trip(storage, name):
     w = synthetic.layered_survey(80, 64, 48, nt=60)
