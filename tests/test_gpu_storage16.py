@@ -158,6 +158,33 @@ def test_storage_modes_against_oracle_to_1000_steps():
         done = c
 
 
+@pytest.mark.parametrize("shape", [(64, 16, 1), (64, 16, 3), (70, 17, 6), (128, 16, 2)])
+@pytest.mark.parametrize("storage,name", MODES)
+def test_thin_and_minimal_grids(storage, name, shape):
+    """The smallest grids 16-bit storage accepts (nx >= 64, ny >= 16), down to
+    one plane, ragged in x and y: 30 steps against the FP64 oracle."""
+    nx, ny, nz = shape
+    vel = synthetic.smooth_random_velocity((nz, ny, nx), 11, spacing=4)
+    h, dt = 10.0, synthetic.cfl_dt(4500.0, 10.0)
+    src = [(nx // 3, ny // 2, nz // 2, 20.0, 0.04, 1.0)]
+    rec = np.array([[0, 0, 0], [nx - 1, ny - 1, nz - 1], [nx // 2, ny // 3, nz // 2]], np.int32)
+    hd = wsb.ws_create(nx, ny, nz, h, dt)
+    wsb.ws_set_storage(hd, storage)
+    wsb.ws_set_velocity(hd, vel)
+    wsb.ws_set_sponge(hd, 3, 0.1)
+    for s in src:
+        wsb.ws_add_source(hd, *s)
+    wsb.ws_set_receivers(hd, rec, 30)
+    wsb.ws_step(hd, 30)
+    u, _ = wsb.ws_read_field(hd)
+    tr = wsb.ws_read_traces(hd)
+    ref = oracle.run(vel.astype(np.float64), h, dt, 30, sources=src, receivers=rec, sponge=(3, 0.1))
+    bound = {"fp16": 3e-3, "bf16": 2.5e-2}[name]
+    err = np.linalg.norm(u - ref["u"]) / np.linalg.norm(ref["u"])
+    assert err <= bound, err
+    assert np.abs(tr - ref["traces"]).max() <= bound * np.abs(ref["traces"]).max()
+
+
 @pytest.mark.parametrize("storage,name", MODES)
 def test_storage_round_trip(storage, name):
     w = synthetic.layered_survey(80, 64, 48, nt=60)
