@@ -244,7 +244,8 @@ int ws_forward(ws_t ws);
  * (V dt/h)^2 as FP16: 10 bytes per cell update instead of 16. Arithmetic
  * stays FP32. U and D share one power-of-two scale per step, picked on the
  * device from max|u^n| and the source amplitude so that the field's maximum
- * sits near 2^12 (16x under the FP16 limit). The current state is converted
+ * sits near 2^12 (16x under the FP16 limit); FP16 then holds values down to
+ * ~2^-36 of that maximum and smaller ones as zero. The current state is converted
  * (rounded once). 16-bit storage runs its own streaming kernel with a 64x16
  * tile and needs nx >= 64, ny >= 16, else BADARG. ws_read_field, ws_write_field
  * and ws_energy convert to and from FP32 (ws_energy then uses the FP32
