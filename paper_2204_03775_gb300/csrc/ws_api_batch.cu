@@ -383,7 +383,8 @@ int ws_batch_create(ws_batch_t *out, int nshots, const ws_t *shots) {
         return cuda_fail(e, "ws_batch_create");
     }
     // online tuning candidates: every tile that fits every shot, z-blocks
-    // for 1, 2, 4, 8 x the resident CTAs and the per-shot default
+    // for about 1, 2, 3, 4, 6 x the resident CTAs in items and the per-shot
+    // default (0)
     for (const auto &tc : kTileCands) {
         bool fits = true;
         for (ws_t ws : b->shots) fits = fits && ws->g.nx >= tc[0] && ws->g.ny >= tc[1];

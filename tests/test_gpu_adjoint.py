@@ -200,6 +200,13 @@ def test_errors():
     with pytest.raises(wsb.WaveStepError) as e:        # too fast for dt
         wsb.ws_set_slowness2(hd, np.full((16, 20, 40), 1e-9, np.float32))
     assert e.value.code == wsb.WS_ERR_CFL
+    h16 = wsb.ws_create(64, 16, 8, 10.0, 1e-3)             # the adjoint needs FP32 storage
+    wsb.ws_set_storage(h16, wsb.WS_STORAGE_FP16)
+    wsb.ws_set_velocity(h16, np.full((8, 16, 64), 2000.0, np.float32))
+    wsb.ws_set_receivers(h16, [[1, 1, 1]], 5)
+    with pytest.raises(wsb.WaveStepError) as e:
+        wsb.ws_adjoint_gradient(h16, data)
+    assert e.value.code == wsb.WS_ERR_STATE
 
 
 def test_autograd_function_two_shots():

@@ -145,6 +145,12 @@ def test_batch_errors():
     assert e.value.code == wsb.WS_ERR_STATE
     with pytest.raises(wsb.WaveStepError):
         wsb.ws_batch_set_tiling(b, 48, 8, 0)
+    h16 = _handle(_shot((72, 40, 30), 2, 10))                # batches need FP32 storage
+    wsb.ws_set_storage(h16, wsb.WS_STORAGE_FP16)
+    b16 = wsb.ws_batch_create([h16])
+    with pytest.raises(wsb.WaveStepError) as e:
+        wsb.ws_batch_step(b16, 1)
+    assert e.value.code == wsb.WS_ERR_STATE
 
 
 def test_full_size_batch_equals_single_shots():
