@@ -341,6 +341,21 @@ int ws_synchronize(ws_t ws);
  * waiting, records the status and drains its own copies. */
 int ws_test_stall(ws_t ws, int item);
 
+/* Test hooks for memory-safety checks (the paper has no counterpart; they
+ * stand in for a sanitizer). A padded field is the interior, the 4-cell
+ * zero halo and, in x, row padding beyond the halo. ws_test_fill_padding
+ * writes a quiet NaN (FP32 0x7fc00000; 16-bit buffers: the format's NaN)
+ * into the row padding of every field buffer of the handle (state and
+ * model; with 16-bit storage the 16-bit ones too) and synchronizes. A later
+ * ws_test_check_padding stores in *bad the number of cells that no longer
+ * hold what they must: 0 in the halo, the NaN in the padding (bit
+ * patterns); it synchronizes the handle's stream. With the padding filled,
+ * the interior results must not change: nothing beyond the halo may reach
+ * a result. ws_write_field and the setters re-zero the whole field, so fill
+ * after them. Errors: BADARG (NULL), CUDA, OOM. */
+int ws_test_fill_padding(ws_t ws);
+int ws_test_check_padding(ws_t ws, long long *bad);
+
 /* Number of kernel launches issued by this handle since creation. */
 long long ws_launch_count(ws_t ws);
 

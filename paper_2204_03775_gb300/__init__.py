@@ -17,5 +17,5 @@ from .binding import (  # noqa: F401
     ws_energy_noalloc,
     ws_get_step, ws_last_error, ws_launch_count, ws_read_field, ws_read_traces, ws_set_kernel,
     ws_set_receivers, ws_set_slowness2, ws_set_sponge, ws_set_storage, ws_set_stream, ws_set_velocity, ws_step,
-    ws_synchronize, ws_test_stall,
+    ws_synchronize, ws_test_check_padding, ws_test_fill_padding, ws_test_stall,
     ws_write_field)

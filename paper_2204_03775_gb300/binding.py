@@ -90,6 +90,8 @@ def load_library(build_if_missing: bool = False):
         "ws_last_error": (ctypes.c_char_p, []),
         "ws_autotune": (i, [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]),
         "ws_test_stall": (i, [vp, i]),
+        "ws_test_fill_padding": (i, [vp]),
+        "ws_test_check_padding": (i, [vp, ctypes.POINTER(ll)]),
         "ws_batch_create": (i, [ctypes.POINTER(vp), i, vp]),
         "ws_batch_destroy": (i, [vp]),
         "ws_batch_set_tiling": (i, [vp, i, i, i]),
@@ -378,6 +380,18 @@ def ws_batch_launch_count(b: Batch) -> int:
 def ws_test_stall(ws: Handle, item: int) -> None:
     """Test hook: the next streaming step withholds one copy of work item `item` (see header)."""
     _check(load_library().ws_test_stall(ws.ptr, int(item)), "ws_test_stall")
+
+
+def ws_test_fill_padding(ws: Handle) -> None:
+    """Write NaN canaries into the row padding of every field buffer (test hook)."""
+    _check(load_library().ws_test_fill_padding(ws.ptr), "ws_test_fill_padding")
+
+
+def ws_test_check_padding(ws: Handle) -> int:
+    """Cells outside the interior that changed since the canaries were written."""
+    n = ctypes.c_longlong(0)
+    _check(load_library().ws_test_check_padding(ws.ptr, ctypes.byref(n)), "ws_test_check_padding")
+    return int(n.value)
 
 
 def ws_launch_count(ws: Handle) -> int:

@@ -373,6 +373,73 @@ void destroy(ws_t ws) {
 
 using namespace wsh;
 
+namespace {
+
+// Padding canaries (test hooks). A padded field is the interior, the 4-cell
+// zero halo around it, and the row padding beyond the halo in x; no kernel
+// may write outside the interior, and nothing read beyond the halo may reach
+// a result.
+__device__ __forceinline__ int pad_class(const ws::Geom &g, long long idx) {
+    const int x = (int)(idx % g.pnx);
+    const long long r = idx / g.pnx;
+    const int y = (int)(r % g.pny), z = (int)(r / g.pny);
+    const bool ix = x >= ws::kXOff && x < ws::kXOff + g.nx;
+    const bool iy = y >= ws::kHalo && y < g.ny + ws::kHalo;
+    const bool iz = z >= ws::kHalo && z < g.nz + ws::kHalo;
+    if (ix && iy && iz) return 0;                                     // interior
+    const bool hx = x >= ws::kXOff - ws::kHalo && x < ws::kXOff + g.nx + ws::kHalo;
+    return (hx && y < g.ny + 2 * ws::kHalo && z < g.nz + 2 * ws::kHalo) ? 1 : 2;   // halo : padding
+}
+
+template <class T>
+__global__ void fill_pad_kernel(T *f, ws::Geom g, T canary) {
+    const long long n = (long long)g.pnx * g.pny * g.pnz;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
+         idx += (long long)gridDim.x * blockDim.x)
+        if (pad_class(g, idx) == 2) f[idx] = canary;
+}
+
+// Cells that differ from what they must hold: 0 in the halo, the canary in
+// the padding (bit patterns).
+template <class T>
+__global__ void check_pad_kernel(const T *f, ws::Geom g, T canary, unsigned long long *bad) {
+    const long long n = (long long)g.pnx * g.pny * g.pnz;
+    unsigned long long c = 0;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int k = pad_class(g, idx);
+        if ((k == 1 && f[idx] != T(0)) || (k == 2 && f[idx] != canary)) ++c;
+    }
+    if (c) atomicAdd(bad, c);
+}
+
+constexpr uint32_t kCanary32 = 0x7fc00000u;   // FP32 quiet NaN
+constexpr uint16_t kCanaryF16 = 0x7e00u;      // FP16 quiet NaN
+constexpr uint16_t kCanaryBf16 = 0x7fc0u;     // BF16 quiet NaN
+
+// Every field buffer of the handle with its canary: the FP32 state and
+// model, and with 16-bit storage the 16-bit state and model too.
+template <class F>
+int for_each_field(ws_t ws, F &&fn) {
+    const uint16_t c16 = ws->storage == WS_STORAGE_BF16 ? kCanaryBf16 : kCanaryF16;
+    for (float *f : {ws->buf[0], ws->buf[1], ws->w}) {
+        int rc = fn(reinterpret_cast<uint32_t *>(f), kCanary32);
+        if (rc != WS_OK) return rc;
+    }
+    if (ws->storage != WS_STORAGE_FP32) {
+        for (uint16_t *f : {ws->buf16[0], ws->buf16[1], ws->d16}) {
+            int rc = fn(f, c16);
+            if (rc != WS_OK) return rc;
+        }
+        return fn(ws->w16, kCanaryF16);
+    }
+    return WS_OK;
+}
+
+constexpr int kPadGrid = 1216, kPadBlock = 256;
+
+}  // namespace
+
 extern "C" {
 
 const char *ws_last_error(void) { return g_err; }
@@ -802,5 +869,42 @@ int ws_test_stall(ws_t ws, int item) {
 }
 
 long long ws_launch_count(ws_t ws) { return ws ? ws->launches : -1; }
+
+int ws_test_fill_padding(ws_t ws) {
+    if (!ws) return fail(WS_ERR_BADARG, "ws_test_fill_padding: NULL handle");
+    int rc = for_each_field(ws, [&](auto *f, auto canary) {
+        fill_pad_kernel<<<kPadGrid, kPadBlock, 0, ws->stream>>>(f, ws->g, canary);
+        ws->launches++;
+        cudaError_t e = cudaGetLastError();
+        return e == cudaSuccess ? WS_OK : cuda_fail(e, "ws_test_fill_padding");
+    });
+    if (rc != WS_OK) return rc;
+    WS_CUDA(cudaStreamSynchronize(ws->stream), "ws_test_fill_padding");
+    return WS_OK;
+}
+
+int ws_test_check_padding(ws_t ws, long long *bad) {
+    if (!ws || !bad) return fail(WS_ERR_BADARG, "ws_test_check_padding: NULL argument");
+    unsigned long long *d = nullptr;
+    WS_CUDA(cudaMalloc(&d, sizeof *d), "ws_test_check_padding");
+    cudaError_t e = cudaMemsetAsync(d, 0, sizeof *d, ws->stream);
+    int rc = e == cudaSuccess ? WS_OK : cuda_fail(e, "ws_test_check_padding");
+    if (rc == WS_OK)
+        rc = for_each_field(ws, [&](auto *f, auto canary) {
+            check_pad_kernel<<<kPadGrid, kPadBlock, 0, ws->stream>>>(f, ws->g, canary, d);
+            ws->launches++;
+            cudaError_t e2 = cudaGetLastError();
+            return e2 == cudaSuccess ? WS_OK : cuda_fail(e2, "ws_test_check_padding");
+        });
+    unsigned long long h = 0;
+    if (rc == WS_OK) {
+        e = cudaMemcpyAsync(&h, d, sizeof h, cudaMemcpyDeviceToHost, ws->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ws->stream);
+        if (e != cudaSuccess) rc = cuda_fail(e, "ws_test_check_padding");
+    }
+    cudaFree(d);
+    if (rc == WS_OK) *bad = (long long)h;
+    return rc;
+}
 
 }  // extern "C"
