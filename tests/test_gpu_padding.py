@@ -107,3 +107,30 @@ def test_batch_with_padding_canaries():
             np.testing.assert_array_equal(x, y)
         assert wsb.ws_test_check_padding(h) == 0
     wsb.ws_batch_destroy(b)
+
+
+def test_adjoint_with_padding_canaries():
+    """The gradient (forward with checkpoints, recomputation, adjoint steps,
+    imaging) from a handle whose state and model carry padding canaries. The
+    gradient restarts the state from rest, re-zeroing both state buffers
+    whole (as ws_write_field does), so afterwards exactly those two buffers'
+    padding differs from the canaries and the model's canaries must be
+    intact; the gradient must be bit for bit the one without canaries."""
+    vel = synthetic.smooth_random_velocity((NZ, NY, NX), 24, 2000.0, 3200.0, spacing=4)
+    dt = synthetic.cfl_dt(float(vel.max()), 10.0)
+    resid = np.random.default_rng(24).standard_normal((4, NT)).astype(np.float32)
+    plain = _handle(wsb.WS_STORAGE_FP32, wsb.WS_KERNEL_STREAM, (64, 8), vel, dt)
+    g_plain, _ = wsb.ws_adjoint_gradient(plain, resid, wsb.WS_ADJ_RESIDUAL)
+
+    rezeroed = _handle(wsb.WS_STORAGE_FP32, wsb.WS_KERNEL_STREAM, (64, 8), vel, dt)
+    wsb.ws_test_fill_padding(rezeroed)
+    wsb.ws_write_field(rezeroed, None, None, 0)
+    expected = wsb.ws_test_check_padding(rezeroed)
+    assert expected > 0
+
+    h = _handle(wsb.WS_STORAGE_FP32, wsb.WS_KERNEL_STREAM, (64, 8), vel, dt)
+    wsb.ws_test_fill_padding(h)
+    g, _ = wsb.ws_adjoint_gradient(h, resid, wsb.WS_ADJ_RESIDUAL)
+    assert wsb.ws_test_check_padding(h) == expected
+    np.testing.assert_array_equal(g, g_plain)
+    assert np.isfinite(g).all() and np.abs(g).max() > 0
