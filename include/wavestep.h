@@ -351,10 +351,11 @@ int ws_test_stall(ws_t ws, int item);
  * hold what they must: 0 in the halo, the NaN in the padding (bit
  * patterns); it synchronizes the handle's stream. With the padding filled,
  * the interior results must not change: nothing beyond the halo may reach
- * a result. Calls that rewrite whole buffers clear the canaries: fill after
- * them (ws_write_field, ws_forward and ws_adjoint_gradient restart the
- * state from rest; ws_set_velocity and ws_set_slowness2 rewrite the model;
- * ws_set_storage converts the state). Errors: BADARG (NULL), CUDA, OOM. */
+ * a result. Calls that zero whole state buffers clear their canaries, so
+ * fill after them: ws_write_field, ws_forward and ws_adjoint_gradient
+ * (which restart from rest) and ws_set_storage (which allocates the 16-bit
+ * buffers); the model setters write the interior only. Errors: BADARG
+ * (NULL), CUDA, OOM. */
 int ws_test_fill_padding(ws_t ws);
 int ws_test_check_padding(ws_t ws, long long *bad);
 
