@@ -231,6 +231,20 @@ int upload_profiles(ws_t ws) {
     for (int i = 0; i < g.nx; ++i) px[i] = (float)taper(i, g.nx, ws->nb, ws->a);
     for (int j = 0; j < g.ny; ++j) py[j] = (float)taper(j, g.ny, ws->nb, ws->a);
     for (int k = 0; k < g.nz; ++k) pz[k] = (float)taper(k, g.nz, ws->nb, ws->a);
+    // the cells of each axis whose factor is exactly 1 (a contiguous middle
+    // range: the profile rises monotonically from both faces)
+    auto ones = [](const std::vector<float> &p, int *lo, int *hi) {
+        const int n = (int)p.size();
+        int a = 0;
+        while (a < n && p[a] != 1.0f) ++a;
+        int b = a;
+        while (b < n && p[b] == 1.0f) ++b;
+        *lo = a;
+        *hi = b;
+    };
+    ones(px, &ws->free16.x0, &ws->free16.x1);
+    ones(py, &ws->free16.y0, &ws->free16.y1);
+    ones(pz, &ws->free16.z0, &ws->free16.z1);
     WS_CUDA(cudaMemcpyAsync(ws->gx, px.data(), 4 * px.size(), cudaMemcpyHostToDevice, ws->stream),
             "upload taper");
     WS_CUDA(cudaMemcpyAsync(ws->gy, py.data(), 4 * py.size(), cudaMemcpyHostToDevice, ws->stream),
@@ -735,7 +749,8 @@ int ws_step(ws_t ws, int nsteps) {
             ws->stall_item = -1;
             cudaError_t e = ws::launch_step_stream16(
                 ws->storage, &ws->t16_halo[ws->cur], &ws->t16_d, &ws->t16_w,
-                ws->buf16[1 - ws->cur], ws->d16, a, ws->scale, ws->step, (float)hint, tiling,
+                ws->buf16[1 - ws->cur], ws->d16, a, ws->scale, ws->step, (float)hint, ws->free16,
+                tiling,
                 ws->nrec > 0 ? ws->rec_ptr : nullptr, ws->rec_entries, ws->stream);
             a.stall_item = -1;
             ws->launches++;

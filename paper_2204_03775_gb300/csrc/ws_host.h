@@ -95,6 +95,7 @@ struct ws_handle {
     ws::Scale16 *scale = nullptr;
     CUtensorMap t16_halo[2], t16_d, t16_w;
     double wmax = 0.0;         // max (V dt / h)^2 of the model
+    ws::Free16 free16{};       // cells whose taper is exactly 1, per axis
 
     // device scratch of ws_adjoint_gradient, kept for the next call
     struct AdjointCache *adj = nullptr;

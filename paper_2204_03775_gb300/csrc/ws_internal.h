@@ -163,6 +163,17 @@ struct Scale16 {
     int e[4];
     unsigned amax[4];
 };
+// Stencil weights of the 16-bit kernel (centre weight c0 applied once; see
+// zero_sum_weights16) and the cells whose taper is exactly 1 on each axis,
+// [x0, x1) x [y0, y1) x [z0, z1) (empty ranges allowed): tiles inside them take
+// the update without taper multiplies, which gives the same bits.
+struct Weights16 {
+    float c0, c1, c2, c3, c4;
+};
+struct Free16 {
+    int x0, x1, y0, y1, z0, z1;
+};
+Weights16 zero_sum_weights16();
 bool stream16_tiling_supported(int tx, int ty);
 // tmap_u: U (16-bit) with box (tx+16, ty+8, 1); tmap_d: D and tmap_w: the
 // 16-bit model, both with box (tx, ty, 1). u_out receives U' (the other U
@@ -172,8 +183,8 @@ bool stream16_tiling_supported(int tx, int ty);
 cudaError_t launch_step_stream16(int storage, const CUtensorMap *tmap_u, const CUtensorMap *tmap_d,
                                  const CUtensorMap *tmap_w, uint16_t *u_out, uint16_t *d_io,
                                  const StepArgs &a, Scale16 *sc, long long step, float src_hint,
-                                 const StreamTiling &t, const int *rec_ptr, const RecEntry *rec,
-                                 cudaStream_t s);
+                                 const Free16 &fr, const StreamTiling &t, const int *rec_ptr,
+                                 const RecEntry *rec, cudaStream_t s);
 // FP32 padded (u^n, u^{n-1}) <-> 16-bit padded (U, D) (interior), exponent slot `slot`.
 cudaError_t launch_encode16(int storage, const float *u, const float *up, uint16_t *U, uint16_t *D,
                             const Geom &g, Scale16 *sc, int slot, cudaStream_t s);
@@ -215,7 +226,6 @@ cudaError_t launch_energy_padded(const float *u, const float *p, const float *w,
 // static device array instead of allocated memory (at most
 // kNoAllocMaxPartials of them). out is a device pointer.
 constexpr int kNoAllocMaxPartials = WS_NOALLOC_MAX_PARTIALS;
-constexpr int kNoAllocMaxDevices = 64;
 cudaError_t launch_energy_noalloc(const float *u, const float *p, const float *v, int nx, int ny,
                                   int nz, double h, double dt, const Coeffs64 &c, double *out,
                                   cudaStream_t s);

@@ -1,53 +1,63 @@
 // Streaming step kernel with 16-bit field storage (BF16 or FP16), velocity form.
 //
-// Same pipeline as the FP32 streaming kernel (one CTA per work item in item
-// order, one TMA producer lane, 9-plane register queue, fused
-// taper/source/receivers), but the state is stored as
+// The state is stored as
 //     U = u^n   and   D = u^n - u^{n-1}   (16 bits each),
 // and the model as FP16 of (V dt/h)^2 * 2^kW16Exp: 10 bytes per cell update
-// (read U, D, W; write U', D'). All arithmetic is FP32; the step computes
-// u^{n-1} = U - D and the same tapered leapfrog update as the FP32 kernels.
+// (read U, D, W; write U', D'). All arithmetic is FP32: the step computes
+// d~ = u^{n+1} - u^n of the tapered leapfrog update (Eq. 2 with the taper)
+// and u~ = u^n + d~, and stores their 16-bit roundings.
 //
 // Why the velocity form: rounding u^{n+1} and keeping it as the next step's
 // u^{n-1} makes every rounding error a kick to the discrete velocity
 // u^n - u^{n-1}, and kicks integrate (relative error ~ N^1.5 eps over N
-// steps). Storing D' = u~^{n+1} - u^n (from the unrounded new value) leaves
+// steps). Storing D' = d~ (computed in FP32, not from the rounded U') leaves
 // the rounding of U' in the displacement only, and the velocity carries just
 // the rounding of D', which is an order of magnitude smaller than |u|.
 //
-// Ring A holds U of plane k with its halo ((TX+16) x (TY+8), 16-bit), ring B
-// the D and W tiles of plane k. U is double-buffered (U' goes to the other
-// buffer: neighbours still read U); D is updated in place (only the thread
-// that computes a cell reads its D).
-//
-// Instruction issue, not memory, limits a 16-bit stencil, so every value is
-// decoded once: a thread decodes its own cells of plane k+4 into its register
-// queue, and at plane k writes them (FP32) into a double-buffered staging
-// tile; the cells around the tile that the star stencil reads (not the
-// corners) are decoded into the same tile, 4 cells per consumer thread above
-// and below the tile and 4 per lane of the last warp beside it. The consumer
-// warps then agree at a named barrier that also ANDs their "no
-// wait failed" flags (so a bounded wait that gives up stops every consumer
-// warp at the same plane) and read their x/y neighbours from the staging tile
-// with 128-bit loads. Each thread computes 4 x-cells of two rows.
+// A 16-bit stencil is bound by instruction issue long before HBM, so the
+// kernel is built to execute few instructions per cell:
+//  - one CTA per work item (a 64 x 16 tile over a block of planes), 4 warps,
+//    every thread computes 4 x-cells of two rows; no producer warp. Thread 0
+//    (ring A: U with its halo) and thread 32 (ring B: the D and W tiles)
+//    issue the TMA copies (cp.async.bulk.tensor) of later planes right after
+//    each plane's barrier, which is the point where every thread is done with
+//    the slots being refilled: no "empty" barriers, no polling producer. Each
+//    slot has a "full" mbarrier (transaction bytes).
+//  - ring A has 9 slots and the z loop runs 9 planes per trip, so ring slots,
+//    mbarrier phases and the 9-plane register queue indices are compile-time
+//    constants (no queue rotation); ring B has 3 slots.
+//  - every value is decoded once: a thread decodes its own cells of plane
+//    k+4 into its register queue and, at plane k, writes them as FP32 into a
+//    double-buffered staging tile; the cells around the tile that the star
+//    stencil reads (not the corners) are decoded into the same tile, 4 cells
+//    per thread above and below the tile and 4 per lane of the last warp
+//    beside it. One barrier per plane (which also ANDs the threads' "no wait
+//    failed" flags, so a bounded wait that gives up stops every warp at the
+//    same plane) separates the staging writes from the neighbour reads
+//    (128-bit loads).
+//  - the stencil sum is c0 u + sum_m c_m s_m with weights whose sum is exact
+//    (zero_sum_weights16: no mass term), symmetric pairs first, two cells per
+//    packed FP32x2 instruction.
+//  - tiles whose cells all have taper 1 (the interior of the absorbing
+//    layer) take d~ = W L + d on planes whose z taper is 1, without the taper
+//    multiplies; the tapered form gives the same bits there.
+//  - 152 registers, 3 CTAs (12 warps) per SM.
 //
 // One power-of-two scale per step for U' and D' (|d| <= |u^{n+1}| + |u^n|,
 // so the same exponent bounds both): stored values are value * 2^e, with e
-// chosen on the device from max |u^n| (accumulated by the previous step) and
-// a host bound on the source term, putting the field's largest value near
-// 2^12, 16x below the FP16 maximum; exponents and maxima live in a 4-slot
-// ring (Scale16) indexed by step, so no host synchronization is needed.
+// chosen on the device from max |u^n| (accumulated by the previous step from
+// the stored U', with packed 16-bit abs-max instructions) and a host bound
+// on the source term, putting the field's largest value near 2^12, 16x below
+// the FP16 maximum; exponents and maxima live in a 4-slot ring (Scale16)
+// indexed by step, so no host synchronization is needed.
 //
-// Decoding is exact and cheap: both formats go through the hardware
-// conversion, one instruction per value (for FP16 measured 6% faster than
-// rebuilding the FP32 bits with integer logic; for BF16, whose bits are the
-// upper half of an FP32, the same speed as shifts and masks but 2 registers
-// fewer, which removed a spill). The kernel computes on the stored values:
-// every input of one field carries the same power-of-two factor, the model's
-// factor 2^kW16Exp is folded into the stencil weights, and the factors meet
-// in exact power-of-two multiplies. Results are rounded to 16 bits once,
-// when stored.
+// Decoding is exact: both formats go through the hardware conversion, one
+// instruction per value. The kernel computes on the stored values: every
+// input of one field carries the same power-of-two factor, the model's factor
+// 2^kW16Exp is folded into the stencil weights, and the factors meet in exact
+// power-of-two multiplies. Results are rounded to 16 bits once, when stored.
 #include <climits>
+#include <cmath>
 
 #include "ws_ptx.cuh"
 
@@ -90,6 +100,17 @@ struct Bf16Fmt {
         asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r.y) : "f"(f.w), "f"(f.z));
         return r;
     }
+    // running max of the magnitudes of two packed values (the sign bits of
+    // the result are those of the operands' xor: meaningless, ignored)
+    static __device__ __forceinline__ unsigned amax(unsigned acc, unsigned w) {
+        unsigned r;
+        asm("max.xorsign.abs.bf16x2 %0, %1, %2;" : "=r"(r) : "r"(acc), "r"(w));
+        return r;
+    }
+    static __device__ __forceinline__ float amax_value(unsigned acc) {
+        const float2 v = two(acc);
+        return fmaxf(fabsf(v.x), fabsf(v.y));
+    }
 };
 
 struct Fp16Fmt {
@@ -103,17 +124,31 @@ struct Fp16Fmt {
         asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(r.y) : "f"(f.w), "f"(f.z));
         return r;
     }
+    static __device__ __forceinline__ unsigned amax(unsigned acc, unsigned w) {
+        unsigned r;
+        asm("max.xorsign.abs.f16x2 %0, %1, %2;" : "=r"(r) : "r"(acc), "r"(w));
+        return r;
+    }
+    static __device__ __forceinline__ float amax_value(unsigned acc) {
+        const float2 v = f16x2_to_f32(acc);
+        return fmaxf(fabsf(v.x), fabsf(v.y));
+    }
 };
 
-// Two rows per thread: a consumer thread computes the 4 x-cells i..i+3 of the
-// rows j and j+1, so the per-plane costs of a thread (ring waits, barrier,
-// loads of the x neighbours, bookkeeping) are spread over 8 cells and the y
-// neighbours rows j-4..j-1 and j+2..j+5 serve both rows.
+// Tile geometry of the 16-bit kernel. A thread computes the 4 x-cells
+// i..i+3 of the rows j and j+1, so its per-plane costs (waits, the barrier,
+// the loads of the x neighbours, bookkeeping) are spread over 8 cells and the
+// y neighbours j-4..j-1 and j+2..j+5 serve both rows. Every thread computes:
+// there is no producer warp. Ring A (U of a plane with its halo) holds NA
+// planes, ring B (the D and W tiles of a plane) NB planes; a plane is
+// processed per loop step and NU = NA planes per loop trip, so every ring
+// slot and register-queue index is a compile-time constant (no queue
+// rotation, no slot arithmetic).
 template <int TX, int TY, int NA, int NB>
 struct Cfg16 {
     static constexpr int kCols = TX / 4;               // threads across a row
-    static constexpr int kConsumers = kCols * (TY / 2);
-    static constexpr int kThreads = kConsumers + 32;
+    static constexpr int kThreads = kCols * (TY / 2);
+    static constexpr int kWarps = kThreads / 32;
     static constexpr int kLead = 8;                    // halo box starts 8 cells left: 16-byte x
     static constexpr int kRowW = TX + 2 * kLead;       // elements per ring-A row
     static constexpr int kRows = TY + 2 * kHalo;
@@ -127,13 +162,13 @@ struct Cfg16 {
     static constexpr int kSW = TX + 2 * kHalo;
     static constexpr int kStage = kSW * kRows;
     // halo cells decoded per plane, in units of 4 cells: 2*TX units in the 8
-    // rows above and below the tile (one per consumer thread), 2*TY = 32
-    // units beside it (the last consumer warp, one per lane)
-    static constexpr int kSideWarp = kConsumers / 32 - 1;
-    static_assert(kConsumers % 32 == 0, "whole consumer warps");
+    // rows above and below the tile (one per thread), 2*TY = 32 units beside
+    // it (the last warp, one per lane)
+    static constexpr int kSideWarp = kWarps - 1;
+    static_assert(kThreads % 32 == 0, "whole warps");
     static_assert(TX % 64 == 0 && TY == 16, "64-wide tiles of 16 rows (8 row pairs)");
-    static_assert(2 * TX == kConsumers && 2 * TY == 32, "one band unit per thread, one side warp");
-    static_assert((NA & (NA - 1)) == 0 && NA >= 8 && (NB & (NB - 1)) == 0 && NB >= 2, "rings");
+    static_assert(2 * TX == kThreads && 2 * TY == 32, "one band unit per thread, one side warp");
+    static_assert(NA == 9 && NB == 3, "ring slots are compile-time constants of a 9-plane trip");
     static_assert(kSlotABytes % 128 == 0 && kSlotBBytes % 128 == 0 && (kStage * 4) % 128 == 0,
                   "slots stay 128-byte aligned");
     static constexpr size_t kSmem =
@@ -147,22 +182,18 @@ __device__ __forceinline__ void sts4(float *p, float4 v) {
                  : "memory");
 }
 
-// Named barrier 1 over the consumer threads that also ANDs their flags.
-__device__ __forceinline__ bool consumers_all(bool ok, int nthreads) {
-    unsigned r;
-    asm volatile(
-        "{\n\t.reg .pred p, q;\n\t"
-        "setp.ne.u32 p, %1, 0;\n\t"
-        "barrier.cta.red.and.pred q, 1, %2, p;\n\t"
-        "selp.u32 %0, 1, 0, q;\n\t}"
-        : "=r"(r)
-        : "r"((unsigned)ok), "r"(nthreads)
-        : "memory");
-    return r != 0;
-}
-
 struct Maps16 {
     CUtensorMap u, d, w;
+};
+
+// Barriers of one CTA: a "full" mbarrier per ring slot (transaction bytes);
+// no "empty" barriers: a slot is refilled right after the plane barrier
+// that follows its last read.
+template <int NA, int NB>
+struct Bars16 {
+    uint64_t fullA[NA], fullB[NB];
+    int issuedA[NA], issuedB[NB];   // copies issued into each slot (for the drain)
+    int abort;
 };
 
 // 2^e as a float, e clamped to the normal range.
@@ -188,9 +219,9 @@ __device__ __forceinline__ int scale_exponent(float a) {
 // Receivers of a two-row thread: RecEntry.lane = 4 * row + x cell. Lane q of
 // the warp takes entry cur + q, fetches the owner's 8 values by shuffle and
 // stores the one it names.
-__device__ __forceinline__ void record_plane2(const float4 (&out)[2], float scale, int k, int *rcur,
-                                              int rend, int *rnext_k, const RecEntry *rec,
-                                              float *traces, int nt_max, long long trace_step) {
+__device__ __forceinline__ void record_plane2(const float4 (&out)[2], int k, int *rcur, int rend,
+                                              int *rnext_k, const RecEntry *rec, float *traces,
+                                              int nt_max, long long trace_step) {
     const int lane = threadIdx.x & 31;
     int cur = *rcur;
     for (;;) {
@@ -212,7 +243,7 @@ __device__ __forceinline__ void record_plane2(const float4 (&out)[2], float scal
 #pragma unroll
             for (int l = 1; l < 8; ++l)
                 if (e.lane == l) x = v[l];
-            traces[(long long)e.r * nt_max + trace_step] = x * scale;
+            traces[(long long)e.r * nt_max + trace_step] = x;
         }
         const int n = __popc(__ballot_sync(0xffffffffu, take));
         cur += n;
@@ -222,14 +253,14 @@ __device__ __forceinline__ void record_plane2(const float4 (&out)[2], float scal
     *rnext_k = cur < rend ? rec[cur].k : INT_MAX;
 }
 
-// Rarely taken paths of a plane. (Moving them out of line, as calls, to
-// shrink the unrolled loop measured 2 % slower: the calls cost registers.)
+// Rarely taken paths of a plane, kept as small inlined helpers.
 
-// Sources of this plane inside the thread's 8 cells: u~ += (W h^2 s) in
-// stored units (src_mask: the CTA's sources).
-__device__ __forceinline__ void inject_sources(float4 *un, const float4 *wr, unsigned src_mask,
-                                            const Sources &src, int i, int j, int k, float wtrue,
-                                            float amp2r) {
+// Sources of this plane inside the thread's 8 cells: d~ += W h^2 s in stored
+// units (src_mask: the CTA's sources), i.e. (V_s dt)^2 s(t_n) added to
+// u^{n+1} after the taper.
+__device__ __forceinline__ void inject_sources(float4 *dn, const float4 *wr, unsigned src_mask,
+                                               const Sources &src, int i, int j, int k,
+                                               float wtrue, float amp2r) {
     for (int qs = 0; qs < src.n; ++qs) {
         const SourceSample &ss = src.s[qs];
         if (((src_mask >> qs) & 1u) && ss.k == k) {
@@ -239,8 +270,8 @@ __device__ __forceinline__ void inject_sources(float4 *un, const float4 *wr, uns
 #pragma unroll
                 for (int l = 0; l < 4; ++l)
                     if (ss.i == i + l)
-                        set_comp(un[r], l, fmaf(comp(wr[r], l) * wtrue, ss.amp * amp2r,
-                                                comp(un[r], l)));
+                        set_comp(dn[r], l, fmaf(comp(wr[r], l) * wtrue, ss.amp * amp2r,
+                                                comp(dn[r], l)));
             }
         }
     }
@@ -248,8 +279,8 @@ __device__ __forceinline__ void inject_sources(float4 *un, const float4 *wr, uns
 
 // Stores of a thread with cells outside the grid (nvalid < 4 or no row j+1).
 __device__ __forceinline__ void store_partial(uint16_t *p, long long d_delta, int pitch, uint2 su0,
-                                           uint2 sd0, uint2 su1, uint2 sd1, int nvalid,
-                                           bool row1) {
+                                              uint2 sd0, uint2 su1, uint2 sd1, int nvalid,
+                                              bool row1) {
     const uint2 su[2] = {su0, su1}, sd[2] = {sd0, sd1};
     for (int r = 0; r < (row1 ? 2 : 1); ++r) {
         uint16_t *o = p + r * pitch;
@@ -261,104 +292,78 @@ __device__ __forceinline__ void store_partial(uint16_t *p, long long d_delta, in
     }
 }
 
-// Receivers of plane k (see record_plane2), values in true units; returns
-// the new (cursor, next plane).
+// Receivers of plane k, values u~ in stored units times 2^r2t (true units);
+// returns the new (cursor, next plane).
 __device__ __forceinline__ int2 record16(float4 u0, float4 u1, int r2t, int k, int rcur, int rend,
-                                      const RecEntry *rec, float *traces, int nt_max,
-                                      long long trace_step) {
+                                         const RecEntry *rec, float *traces, int nt_max,
+                                         long long trace_step) {
     const float4 ut[2] = {make_float4(scale2(u0.x, r2t), scale2(u0.y, r2t), scale2(u0.z, r2t),
                                       scale2(u0.w, r2t)),
                           make_float4(scale2(u1.x, r2t), scale2(u1.y, r2t), scale2(u1.z, r2t),
                                       scale2(u1.w, r2t))};
     int next = INT_MAX;
-    record_plane2(ut, 1.0f, k, &rcur, rend, &next, rec, traces, nt_max, trace_step);
+    record_plane2(ut, k, &rcur, rend, &next, rec, traces, nt_max, trace_step);
     return make_int2(rcur, next);
 }
 
+// Per-thread state of the walk down an item.
 struct Walk16 {
-    float4 q[9][2];     // u^n (stored units) of planes k-4 .. k+4, rows j and j+1 (rotated)
-    float gzb[3];       // z taper of planes k, k+1, k+2 (rotated)
-    float4 gxy[2];
-    uint16_t *out_k;    // U' of (i, j, k); D of it at out_k + d_delta, row j+1 one pitch on
-    int nvalid;         // valid x cells of the rows (0: none)
-    bool row1;          // row j+1 inside the grid
-    bool full;          // all 8 cells inside the grid
+    float4 q[9][2];     // u^n (stored units) of planes k-4 .. k+4, rows j and j+1
     int rcur, rend, rnext_k;
-    unsigned src_mask;
-    unsigned gAw, gAr, gB;
-    float amax;         // running max |u~| in stored units
+    unsigned amax;      // running max |U'| (two 16-bit magnitudes, sign bits meaningless)
     bool ok;
 };
 
-// A thread's halo units: ring-A element offset and staging offset of its 4
-// cells above or below the tile, and (last consumer warp) of its 4 cells
-// beside the tile.
-struct Halo {
-    int band_src, band_dst, side_src, side_dst;
+// What a thread needs of its item, fixed over the walk.
+struct Ctx16 {
+    const uint16_t *ringA, *ringB;
+    float *stage;
+    uint16_t *pu;          // U' of (i, j, z0); D at pu + d_delta, row j+1 one pitch on
+    long long d_delta, plane;
+    const float *gz;
+    float4 gxy[2];         // gx * gy of the 4 columns per row (0 outside the grid)
+    int i, j, z0, z1, nb, nplanes;
+    int offA, offB, offS, band_src, band_dst, side_src, side_dst;
+    int pitch, nvalid;
+    bool row1, full, side, xy_free;
+    int fz0, fz1;          // planes whose taper is exactly 1
+    unsigned src_mask;
 };
 
-template <class Fmt, int TX, int TY, int NA, int NB, int NU>
+template <class Fmt, int TX, int TY, int NA, int NB>
 struct Kern16 {
     using Cfg = Cfg16<TX, TY, NA, NB>;
-    using R = Rings<NA, NB>;
+    using B = Bars16<NA, NB>;
 
     // factors of one launch (uniform)
     struct Factors {
-        Coeffs c;       // stencil weights times 2^-kW16Exp: absorbs the model's factor
+        float c0, c1, c2, c3, c4;   // zero-sum weights times 2^-kW16Exp: absorb the model's factor
         float wtrue;    // stored W -> (V dt/h)^2
         float amp2r;    // source amplitude (h^2 s) -> stored U units
-        float ro;       // u~ and u~ - u (stored U units) -> stored U' and D' values
+        float ro;       // stored U units -> the output units of U' and D'
         int r2t;        // stored U units -> true units: times 2^r2t
     };
 
-    static __device__ __forceinline__ bool produce_a(R &rg, uint16_t *ringA, const Maps16 &mp,
-                                                     unsigned g, const Item &it, int pr,
-                                                     unsigned *status) {
-        const int slot = g & (NA - 1);
-        if (!wait_phase(&rg.emptyA[slot], ((g / NA) & 1u) ^ 1u, &rg.abort, status)) return false;
-        rg.issuedA[slot]++;
-        mbar_arrive_expect_tx(&rg.fullA[slot], Cfg::kSlotABytes);
-        // box corner at interior (i0 - 8, j0 - 4, z0 - 4 + pr): padded (i0 + kXOff - 8, j0, z0 + pr)
-        tma_load_3d(ringA + slot * Cfg::kSlotA, &mp.u, &rg.fullA[slot], it.i0 + kXOff - Cfg::kLead,
+    // U of relative plane pr (interior plane z0 - 4 + pr, with its halo) into
+    // ring-A slot `slot`. Box corner: interior (i0 - 8, j0 - 4), padded
+    // (i0 + kXOff - 8, j0, z0 + pr); x is a multiple of 8 elements (16 bytes).
+    static __device__ __forceinline__ void issue_a(B &br, uint16_t *ringA, const Maps16 &mp,
+                                                   const Item &it, int slot, int pr) {
+        br.issuedA[slot]++;
+        mbar_arrive_expect_tx(&br.fullA[slot], Cfg::kSlotABytes);
+        tma_load_3d(ringA + slot * Cfg::kSlotA, &mp.u, &br.fullA[slot], it.i0 + kXOff - Cfg::kLead,
                     it.j0, it.z0 + pr);
-        return true;
     }
 
-    static __device__ __forceinline__ bool produce_b(R &rg, uint16_t *ringB, const Maps16 &mp,
-                                                     unsigned g, const Item &it, int b,
-                                                     unsigned *status) {
-        const int slot = g & (NB - 1);
-        if (!wait_phase(&rg.emptyB[slot], ((g / NB) & 1u) ^ 1u, &rg.abort, status)) return false;
-        rg.issuedB[slot]++;
+    // D and W of interior plane z0 + b into ring-B slot `slot`.
+    static __device__ __forceinline__ void issue_b(B &br, uint16_t *ringB, const Maps16 &mp,
+                                                   const Item &it, int slot, int b) {
+        br.issuedB[slot]++;
         uint16_t *dst = ringB + slot * Cfg::kSlotB;
-        mbar_arrive_expect_tx(&rg.fullB[slot], Cfg::kSlotBBytes);
-        tma_load_3d(dst, &mp.d, &rg.fullB[slot], it.i0 + kXOff, it.j0 + kHalo, it.z0 + b + kHalo);
-        tma_load_3d(dst + Cfg::kTile, &mp.w, &rg.fullB[slot], it.i0 + kXOff, it.j0 + kHalo,
+        mbar_arrive_expect_tx(&br.fullB[slot], Cfg::kSlotBBytes);
+        tma_load_3d(dst, &mp.d, &br.fullB[slot], it.i0 + kXOff, it.j0 + kHalo, it.z0 + b + kHalo);
+        tma_load_3d(dst + Cfg::kTile, &mp.w, &br.fullB[slot], it.i0 + kXOff, it.j0 + kHalo,
                     it.z0 + b + kHalo);
-        return true;
-    }
-
-    static __device__ void producer(R &rg, uint16_t *ringA, uint16_t *ringB, const Maps16 &mp,
-                                    const StepArgs &a, int zb, int tiles_x, int ntiles,
-                                    int nitems) {
-        unsigned gA = 0, gB = 0;
-        for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
-            const Item it = item_of(item, tiles_x, ntiles, zb, a.g.nz, TX, TY);
-            const int nb = it.z1 - it.z0, nplanes = nb + 2 * kHalo;
-            for (int pr = 0; pr < 2 * kHalo; ++pr) {
-                if (pr == 0 && item == a.stall_item) {   // test hook: never filled, so the
-                    ++gA;                                 // consumers' bounded waits run out
-                    continue;
-                }
-                if (!produce_a(rg, ringA, mp, gA++, it, pr, a.status)) return;
-            }
-            for (int b = 0; b < nb; ++b) {
-                if (!produce_b(rg, ringB, mp, gB++, it, b, a.status)) return;
-                if (b + 2 * kHalo < nplanes &&
-                    !produce_a(rg, ringA, mp, gA++, it, b + 2 * kHalo, a.status))
-                    return;
-            }
-        }
     }
 
     // 4 stored values (8 bytes), streaming store.
@@ -367,29 +372,15 @@ struct Kern16 {
                      : "memory");
     }
 
-    static __device__ __forceinline__ Halo halo_units(int tid) {
-        Halo h;
-        const int band = tid / Cfg::kCols, n = tid - band * Cfg::kCols;
-        int y = band < kHalo ? band : TY + band;            // rows 0..3, TY+4..TY+7
-        int c = kHalo + 4 * n;                                // staging column
-        h.band_src = y * Cfg::kRowW + c + (Cfg::kLead - kHalo);
-        h.band_dst = y * Cfg::kSW + c;
-        const int v = tid & 31;
-        y = kHalo + (v >> 1);
-        c = (v & 1) ? TX + kHalo : 0;
-        h.side_src = y * Cfg::kRowW + c + (Cfg::kLead - kHalo);
-        h.side_dst = y * Cfg::kSW + c;
-        return h;
-    }
-
-    // u~ (stored units) of one row's 4 cells: the tapered leapfrog update of the FP32
-    // kernels, in their operation order. yp/ym: rows j+m / j-m of this row.
+    // The stencil sum of one row's 4 cells (two FP32x2 pairs): c0 u +
+    // sum_m c_m s_m, s_m the six neighbours at distance m, each summed as
+    // symmetric pairs first. xl, xr: cells x-4..x-1 and x+4..x+7 of the row;
+    // yp/ym: rows j+m / j-m of this row; z from the register queue.
     template <int RQ>
-    static __device__ __forceinline__ float4 update_row(const Walk16 &wk, int r, const float4 &xl,
-                                                        const float4 &xr, const float4 (&yp)[4],
-                                                        const float4 (&ym)[4], const float4 &dc,
-                                                        const float4 &wr, float gzk,
-                                                        const Factors &fc) {
+    static __device__ __forceinline__ void stencil_row(const Walk16 &wk, int r, const float4 &xl,
+                                                       const float4 &xr, const float4 (&yp)[4],
+                                                       const float4 (&ym)[4], const Factors &fc,
+                                                       float2 (&lap)[2]) {
         const float4 xc = wk.q[(RQ + 4) % 9][r];
         const float e[12] = {xl.x, xl.y, xl.z, xl.w, xc.x, xc.y, xc.z, xc.w,
                              xr.x, xr.y, xr.z, xr.w};
@@ -406,7 +397,6 @@ struct Kern16 {
                 sx[p][m] = make_float2(e[4 + l0 + m] + e[4 + l0 - m], e[4 + l1 + m] + e[4 + l1 - m]);
             }
         }
-        float2 o[2];
 #pragma unroll
         for (int p = 0; p < 2; ++p) {
             float2 s[5];
@@ -417,66 +407,86 @@ struct Kern16 {
                                        pair(wk.q[(RQ + 4 - m + 9) % 9][r], p));
                 s[m] = add2(add2(sx[p][m], sy), sz);
             }
-            const float2 uc = pair(xc, p);
-            // sum_m c_m (s_m - 6 u): exactly zero on constants (see Coeffs)
-            float2 lap = mul2(splat(fc.c.c4), fma2(splat(-6.0f), uc, s[4]));
-            lap = fma2(splat(fc.c.c3), fma2(splat(-6.0f), uc, s[3]), lap);
-            lap = fma2(splat(fc.c.c2), fma2(splat(-6.0f), uc, s[2]), lap);
-            lap = fma2(splat(fc.c.c1), fma2(splat(-6.0f), uc, s[1]), lap);
-            const float2 um = add2(uc, mul2(splat(-1.0f), pair(dc, p)));     // u^{n-1}
-            const float2 gd = mul2(pair(wk.gxy[r], p), splat(gzk));
-            const float2 ngd = mul2(pair(wk.gxy[r], p), splat(-gzk));        // -gd, exactly
-            const float2 t = fma2(pair(wr, p), lap, fma2(splat(2.0f), uc, mul2(ngd, um)));
-            o[p] = mul2(gd, t);                                              // u~
+            float2 l = mul2(splat(fc.c0), pair(xc, p));
+            l = fma2(splat(fc.c4), s[4], l);
+            l = fma2(splat(fc.c3), s[3], l);
+            l = fma2(splat(fc.c2), s[2], l);
+            lap[p] = fma2(splat(fc.c1), s[1], l);
+        }
+    }
+
+    // d~ = u~ - u of one row's 4 cells in velocity form, u^{n-1} = u - d:
+    // u~ = g (2u - g u^{n-1} + W L) gives d~ = g (W L + g d) - (1 - g)^2 u.
+    // With g = 1 (fast) this is W L + d, bit for bit the same value.
+    static __device__ __forceinline__ float4 delta_fast(const float2 (&lap)[2], const float4 &d,
+                                                        const float4 &w) {
+        const float2 a = fma2(lo2(w), lap[0], lo2(d));
+        const float2 b = fma2(hi2(w), lap[1], hi2(d));
+        return make_float4(a.x, a.y, b.x, b.y);
+    }
+    static __device__ __forceinline__ float4 delta_taper(const float2 (&lap)[2], const float4 &d,
+                                                         const float4 &w, const float4 &u,
+                                                         const float4 &gxy, float gzk) {
+        float2 o[2];
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+            const float2 g = mul2(pair(gxy, p), splat(gzk));
+            const float2 t = mul2(g, fma2(pair(w, p), lap[p], mul2(g, pair(d, p))));
+            const float2 gm1 = fma2(pair(gxy, p), splat(gzk), splat(-1.0f));   // g - 1
+            const float2 omg = fma2(pair(gxy, p), splat(-gzk), splat(1.0f));   // 1 - g, exactly -(g - 1)
+            o[p] = fma2(omg, mul2(gm1, pair(u, p)), t);
         }
         return make_float4(o[0].x, o[0].y, o[1].x, o[1].y);
     }
 
+    // Plane k of the walk, RQ = (k - z0) mod 9; tp: parity of the trip.
     template <int RQ>
-    static __device__ __forceinline__ void plane_step(Walk16 &wk, R &rg, const uint16_t *ringA,
-                                                      const uint16_t *ringB, float *stage,
+    static __device__ __forceinline__ void plane_step(Walk16 &wk, const Ctx16 &cx, B &br,
+                                                      uint16_t *ringA_w, uint16_t *ringB_w,
+                                                      const Maps16 &mp, const Item &it,
                                                       const StepArgs &a, const Factors &fc,
-                                                      long long d_delta, const Halo &hu, int k,
-                                                      int i, int j, int offA, int offB, int offS,
+                                                      float *st, int k, unsigned tp,
                                                       const RecEntry *rec) {
         constexpr int Q8 = (RQ + 8) % 9, Q4 = (RQ + 4) % 9;
-        // plane k+4 of this thread's two rows -> the queue
+        constexpr int SA_OWN = (RQ + 8) % NA, SA_HALO = (RQ + 4) % NA, SB = RQ % NB;
+        // fill parities: relative plane r + 8 fills slot SA_OWN for the
+        // (trip + (RQ + 8) / 9)-th time; plane r fills SB for the (3 trip + RQ / 3)-th
+        constexpr unsigned PA = ((RQ + 8) / NA) & 1u, PB = (RQ / NB) & 1u;
+        const int r = k - cx.z0;
+
+        // plane k + 4 of this thread's two rows -> the queue (decoded once)
+        wk.ok = wait_phase(&br.fullA[SA_OWN], tp ^ PA, &br.abort, a.status) && wk.ok;
         {
-            const int slot = wk.gAw & (NA - 1);
-            wk.ok = wait_phase(&rg.fullA[slot], (wk.gAw / NA) & 1u, &rg.abort, a.status) && wk.ok;
-            const uint16_t *p = ringA + slot * Cfg::kSlotA + offA;
+            const uint16_t *p = cx.ringA + SA_OWN * Cfg::kSlotA + cx.offA;
             wk.q[Q8][0] = Fmt::decode(lds2u(p));
             wk.q[Q8][1] = Fmt::decode(lds2u(p + Cfg::kRowW));
-            ++wk.gAw;
         }
-        const int sb = wk.gB & (NB - 1);
-        wk.ok = wait_phase(&rg.fullB[sb], (wk.gB / NB) & 1u, &rg.abort, a.status) && wk.ok;
-        const uint16_t *tb = ringB + sb * Cfg::kSlotB + offB;
-        const float4 dc0 = Fmt::decode(lds2u(tb)), dc1 = Fmt::decode(lds2u(tb + TX));
-        const float4 wr0 = Fp16Fmt::decode(lds2u(tb + Cfg::kTile));
-        const float4 wr1 = Fp16Fmt::decode(lds2u(tb + Cfg::kTile + TX));
-        warp_arrive(&rg.emptyB[sb]);
-        ++wk.gB;
-
-        wk.gzb[(RQ + 2) % 3] = __ldg(a.gz + min(k + 2, a.g.nz - 1));   // past nz: unused
+        // D and W of plane k (raw; decoded where they are used)
+        wk.ok = wait_phase(&br.fullB[SB], tp ^ PB, &br.abort, a.status) && wk.ok;
+        const uint16_t *tb = cx.ringB + SB * Cfg::kSlotB + cx.offB;
+        const uint2 dr0 = lds2u(tb), dr1 = lds2u(tb + TX);
+        const uint2 wr0 = lds2u(tb + Cfg::kTile), wr1 = lds2u(tb + Cfg::kTile + TX);
+        const float gzk = __ldg(cx.gz + k);
 
         // staging tile of plane k: this thread's own two rows (decoded four
-        // planes ago), and its halo unit from the ring; then every consumer
-        // agrees before anyone reads a neighbour
-        float *st = stage + (k & 1) * Cfg::kStage;
-        sts4(st + offS, wk.q[Q4][0]);
-        sts4(st + offS + Cfg::kSW, wk.q[Q4][1]);
+        // planes ago) and its halo unit; then every thread agrees before
+        // anyone reads a neighbour
+        sts4(st + cx.offS, wk.q[Q4][0]);
+        sts4(st + cx.offS + Cfg::kSW, wk.q[Q4][1]);
         {
-            const uint16_t *src = ringA + (wk.gAr & (NA - 1)) * Cfg::kSlotA;
-            sts4(st + hu.band_dst, Fmt::decode(lds2u(src + hu.band_src)));
-            if ((threadIdx.x >> 5) == Cfg::kSideWarp)
-                sts4(st + hu.side_dst, Fmt::decode(lds2u(src + hu.side_src)));
+            const uint16_t *src = cx.ringA + SA_HALO * Cfg::kSlotA;
+            sts4(st + cx.band_dst, Fmt::decode(lds2u(src + cx.band_src)));
+            if (cx.side) sts4(st + cx.side_dst, Fmt::decode(lds2u(src + cx.side_src)));
         }
-        wk.ok = consumers_all(wk.ok, Cfg::kConsumers);
-        warp_arrive(&rg.emptyA[wk.gAr & (NA - 1)]);
-        ++wk.gAr;
+        wk.ok = __syncthreads_and(wk.ok) != 0;
+        if (!wk.ok) return;
+        // every thread is done with ring-A slot SA_HALO (plane k) and ring-B
+        // slot SB: refill them with planes k + 9 (U) and k + 3 (D, W)
+        if (threadIdx.x == 0 && r + 4 + NA < cx.nplanes)
+            issue_a(br, ringA_w, mp, it, SA_HALO, r + 4 + NA);
+        if (threadIdx.x == 32 && r + NB < cx.nb) issue_b(br, ringB_w, mp, it, SB, r + NB);
 
-        const float *row = st + offS;
+        const float *row = st + cx.offS;
         const float4 xl0 = lds4(row - 4), xr0 = lds4(row + 4);
         const float4 xl1 = lds4(row + Cfg::kSW - 4), xr1 = lds4(row + Cfg::kSW + 4);
         // rows j-4..j-1 and j+2..j+5
@@ -486,255 +496,264 @@ struct Kern16 {
             lm[m - 1] = lds4(row - m * Cfg::kSW);
             lp[m - 1] = lds4(row + (m + 1) * Cfg::kSW);
         }
-        const float gzk = wk.gzb[RQ % 3];
-        float4 un[2];
+        float2 lap0[2], lap1[2];
         {
             const float4 yp[4] = {wk.q[Q4][1], lp[0], lp[1], lp[2]};
-            un[0] = update_row<RQ>(wk, 0, xl0, xr0, yp, lm, dc0, wr0, gzk, fc);
+            stencil_row<RQ>(wk, 0, xl0, xr0, yp, lm, fc, lap0);
         }
         {
             const float4 ym[4] = {wk.q[Q4][0], lm[0], lm[1], lm[2]};
-            un[1] = update_row<RQ>(wk, 1, xl1, xr1, lp, ym, dc1, wr1, gzk, fc);
+            stencil_row<RQ>(wk, 1, xl1, xr1, lp, ym, fc, lap1);
         }
-        if (wk.src_mask) {
-            float4 t[2] = {un[0], un[1]};
-            const float4 w[2] = {wr0, wr1};
-            inject_sources(t, w, wk.src_mask, a.src, i, j, k, fc.wtrue, fc.amp2r);
-            un[0] = t[0];
-            un[1] = t[1];
+        const float4 d0 = Fmt::decode(dr0), d1 = Fmt::decode(dr1);
+        const float4 w0 = Fp16Fmt::decode(wr0), w1 = Fp16Fmt::decode(wr1);
+        float4 dn[2];
+        if (cx.xy_free && k >= cx.fz0 && k < cx.fz1) {
+            dn[0] = delta_fast(lap0, d0, w0);
+            dn[1] = delta_fast(lap1, d1, w1);
+        } else {
+            dn[0] = delta_taper(lap0, d0, w0, wk.q[Q4][0], cx.gxy[0], gzk);
+            dn[1] = delta_taper(lap1, d1, w1, wk.q[Q4][1], cx.gxy[1], gzk);
         }
-        // cells outside the grid have zero taper, so zero u~: no guard needed
-        wk.amax = fmaxf(wk.amax, fmaxf(fmaxf(fmaxf(fabsf(un[0].x), fabsf(un[0].y)),
-                                             fmaxf(fabsf(un[0].z), fabsf(un[0].w))),
-                                       fmaxf(fmaxf(fabsf(un[1].x), fabsf(un[1].y)),
-                                             fmaxf(fabsf(un[1].z), fabsf(un[1].w)))));
-        // increments u~ - u, then the stored values of both rows
-        uint2 su[2], sd[2];
+        if (cx.src_mask) {
+            const float4 w[2] = {w0, w1};
+            inject_sources(dn, w, cx.src_mask, a.src, cx.i, cx.j, k, fc.wtrue, fc.amp2r);
+        }
+        float4 un[2];
 #pragma unroll
-        for (int r = 0; r < 2; ++r) {
-            const float4 xc = wk.q[Q4][r];
-            const float2 d0 = add2(lo2(un[r]), make_float2(-xc.x, -xc.y));
-            const float2 d1 = add2(hi2(un[r]), make_float2(-xc.z, -xc.w));
-            const float2 u0 = mul2(lo2(un[r]), splat(fc.ro)), u1 = mul2(hi2(un[r]), splat(fc.ro));
-            const float2 e0 = mul2(d0, splat(fc.ro)), e1 = mul2(d1, splat(fc.ro));
-            su[r] = Fmt::encode(make_float4(u0.x, u0.y, u1.x, u1.y));
-            sd[r] = Fmt::encode(make_float4(e0.x, e0.y, e1.x, e1.y));
+        for (int rr = 0; rr < 2; ++rr) {
+            const float2 a0 = add2(lo2(wk.q[Q4][rr]), lo2(dn[rr]));
+            const float2 a1 = add2(hi2(wk.q[Q4][rr]), hi2(dn[rr]));
+            un[rr] = make_float4(a0.x, a0.y, a1.x, a1.y);
         }
-        if (wk.full) {
-#pragma unroll
-            for (int r = 0; r < 2; ++r) {
-                store16(wk.out_k + r * a.g.pnx, su[r]);
-                store16(wk.out_k + r * a.g.pnx + d_delta, sd[r]);
-            }
-        } else if (wk.nvalid > 0) {
-            store_partial(wk.out_k, d_delta, a.g.pnx, su[0], sd[0], su[1], sd[1], wk.nvalid,
-                          wk.row1);
-        }
-        wk.out_k += a.g.plane;
         if (k == wk.rnext_k) {
             const int2 rc = record16(un[0], un[1], fc.r2t, k, wk.rcur, wk.rend, rec, a.traces,
                                      a.nt_max, a.trace_step);
             wk.rcur = rc.x;
             wk.rnext_k = rc.y;
         }
+        if (fc.ro != 1.0f) {   // the output exponent differs from the input's (rare)
+#pragma unroll
+            for (int rr = 0; rr < 2; ++rr) {
+                const float2 a0 = mul2(lo2(un[rr]), splat(fc.ro)), a1 = mul2(hi2(un[rr]), splat(fc.ro));
+                const float2 b0 = mul2(lo2(dn[rr]), splat(fc.ro)), b1 = mul2(hi2(dn[rr]), splat(fc.ro));
+                un[rr] = make_float4(a0.x, a0.y, a1.x, a1.y);
+                dn[rr] = make_float4(b0.x, b0.y, b1.x, b1.y);
+            }
+        }
+        uint2 su[2], sd[2];
+#pragma unroll
+        for (int rr = 0; rr < 2; ++rr) {
+            su[rr] = Fmt::encode(un[rr]);
+            sd[rr] = Fmt::encode(dn[rr]);
+        }
+        uint16_t *pk = cx.pu + (long long)r * cx.plane;
+        if (cx.full) {
+            store16(pk, su[0]);
+            store16(pk + cx.d_delta, sd[0]);
+            store16(pk + cx.pitch, su[1]);
+            store16(pk + cx.pitch + cx.d_delta, sd[1]);
+        } else if (cx.nvalid > 0) {
+            store_partial(pk, cx.d_delta, cx.pitch, su[0], sd[0], su[1], sd[1], cx.nvalid, cx.row1);
+        }
+        // cells outside the grid have zero taper, so zero u~ (NaN canaries in
+        // the padding are ignored by the max)
+        wk.amax = Fmt::amax(wk.amax, su[0].x);
+        wk.amax = Fmt::amax(wk.amax, su[0].y);
+        wk.amax = Fmt::amax(wk.amax, su[1].x);
+        wk.amax = Fmt::amax(wk.amax, su[1].y);
     }
 
-    // planes kb + RQ .. kb + NU - 1 of a group; false once the item ends
+    // planes kb + RQ .. kb + NA - 1 of a trip; false once the item ends
     template <int RQ>
-    static __device__ __forceinline__ bool planes(Walk16 &wk, R &rg, const uint16_t *ringA,
-                                                  const uint16_t *ringB, float *stage,
+    static __device__ __forceinline__ bool planes(Walk16 &wk, const Ctx16 &cx, B &br,
+                                                  uint16_t *ringA_w, uint16_t *ringB_w,
+                                                  const Maps16 &mp, const Item &it,
                                                   const StepArgs &a, const Factors &fc,
-                                                  long long d_delta, const Halo &hu,
-                                                  const Item &it, int kb, int i, int j, int offA,
-                                                  int offB, int offS, const RecEntry *rec) {
-        if constexpr (RQ < NU) {
-            // wk.ok is the same in every consumer after a staging barrier
-            if (kb + RQ >= it.z1 || !wk.ok) return false;
-            plane_step<RQ>(wk, rg, ringA, ringB, stage, a, fc, d_delta, hu, kb + RQ, i, j, offA,
-                           offB, offS, rec);
-            return planes<RQ + 1>(wk, rg, ringA, ringB, stage, a, fc, d_delta, hu, it, kb, i, j,
-                                  offA, offB, offS, rec);
+                                                  float *st_even, float *st_odd, int kb,
+                                                  unsigned tp, const RecEntry *rec) {
+        if constexpr (RQ < NA) {
+            if (kb + RQ >= cx.z1) return false;
+            plane_step<RQ>(wk, cx, br, ringA_w, ringB_w, mp, it, a, fc,
+                           (RQ & 1) ? st_odd : st_even, kb + RQ, tp, rec);
+            // wk.ok is the same in every thread after the plane barrier
+            if (!wk.ok) return false;
+            return planes<RQ + 1>(wk, cx, br, ringA_w, ringB_w, mp, it, a, fc, st_even, st_odd,
+                                  kb, tp, rec);
         }
         return true;
     }
-
-    static __device__ __forceinline__ void rotate_queue(Walk16 &wk) {
-        if constexpr (NU % 9 != 0) {
-            float4 t[9][2];
-#pragma unroll
-            for (int m = 0; m < 9; ++m) {
-                t[m][0] = wk.q[(m + NU) % 9][0];
-                t[m][1] = wk.q[(m + NU) % 9][1];
-            }
-#pragma unroll
-            for (int m = 0; m < 9; ++m) {
-                wk.q[m][0] = t[m][0];
-                wk.q[m][1] = t[m][1];
-            }
-        }
-        if constexpr (NU % 3 != 0) {
-            const float t0 = wk.gzb[NU % 3], t1 = wk.gzb[(NU + 1) % 3], t2 = wk.gzb[(NU + 2) % 3];
-            wk.gzb[0] = t0;
-            wk.gzb[1] = t1;
-            wk.gzb[2] = t2;
-        }
-    }
-
-    static __device__ __forceinline__ void consumer(R &rg, const uint16_t *ringA,
-                                                    const uint16_t *ringB, float *stage,
-                                                    uint16_t *u_out, long long d_delta,
-                                    const StepArgs &a, const Factors &fc, int zb, int tiles_x,
-                                    int ntiles, int nitems, const int *rec_ptr,
-                                    const RecEntry *rec, unsigned *amax_out) {
-        const Geom &g = a.g;
-        const int tid = threadIdx.x;
-        const int tx = tid % Cfg::kCols;
-        const int py = tid / Cfg::kCols;
-        const int offA = (kHalo + 2 * py) * Cfg::kRowW + Cfg::kLead + 4 * tx;
-        const int offB = 2 * py * TX + 4 * tx;
-        const int offS = (kHalo + 2 * py) * Cfg::kSW + kHalo + 4 * tx;
-        const Halo hu = halo_units(tid);
-        Walk16 wk;
-        wk.gAw = wk.gAr = wk.gB = 0;
-        wk.ok = true;
-        wk.amax = 0.0f;
-        for (int item = blockIdx.x; item < nitems && wk.ok; item += gridDim.x) {
-            const Item it = item_of(item, tiles_x, ntiles, zb, g.nz, TX, TY);
-            const int i = it.i0 + 4 * tx;
-            const int j = it.j0 + 2 * py;
-            const bool col_ok = (j < g.ny) && (i < g.nx);
-            wk.nvalid = col_ok ? min(4, g.nx - i) : 0;
-            wk.row1 = j + 1 < g.ny;
-            wk.full = wk.nvalid == 4 && wk.row1;
-#pragma unroll
-            for (int r = 0; r < 2; ++r) {
-                wk.gxy[r] = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (col_ok && j + r < g.ny) {
-                    const float gyj = a.gy[j + r];
-                    wk.gxy[r].x = a.gx[i] * gyj;
-                    if (wk.nvalid > 1) wk.gxy[r].y = a.gx[i + 1] * gyj;
-                    if (wk.nvalid > 2) wk.gxy[r].z = a.gx[i + 2] * gyj;
-                    if (wk.nvalid > 3) wk.gxy[r].w = a.gx[i + 3] * gyj;
-                }
-            }
-            wk.src_mask = 0u;
-            for (int qs = 0; qs < a.src.n; ++qs) {
-                const SourceSample &ss = a.src.s[qs];
-                if (ss.i >= it.i0 && ss.i < it.i0 + TX && ss.j >= it.j0 && ss.j < it.j0 + TY &&
-                    ss.k >= it.z0 && ss.k < it.z1)
-                    wk.src_mask |= 1u << qs;
-            }
-            wk.rcur = wk.rend = 0;
-            if (rec_ptr != nullptr) {
-                const int r = it.tile * (Cfg::kConsumers / 32) + (tid >> 5);
-                wk.rend = rec_ptr[r + 1];
-                wk.rcur = first_entry(rec, rec_ptr[r], wk.rend, it.z0);
-            }
-            wk.rnext_k = wk.rcur < wk.rend ? rec[wk.rcur].k : INT_MAX;
-            wk.out_k = u_out + pidx(g, col_ok ? i : 0, col_ok ? j : 0, it.z0);
-#pragma unroll
-            for (int d = 0; d < 2; ++d)
-                wk.gzb[d] = (it.z0 + d < g.nz) ? __ldg(a.gz + it.z0 + d) : 1.0f;
-
-#pragma unroll
-            for (int m = 0; m < 2 * kHalo; ++m) {
-                const int slot = wk.gAw & (NA - 1);
-                wk.ok = wk.ok && wait_phase(&rg.fullA[slot], (wk.gAw / NA) & 1u, &rg.abort, a.status);
-                const uint16_t *p = ringA + slot * Cfg::kSlotA + offA;
-                wk.q[m][0] = Fmt::decode(lds2u(p));
-                wk.q[m][1] = Fmt::decode(lds2u(p + Cfg::kRowW));
-                ++wk.gAw;
-            }
-#pragma unroll
-            for (int m = 0; m < kHalo; ++m) {
-                warp_arrive(&rg.emptyA[wk.gAr & (NA - 1)]);
-                ++wk.gAr;
-            }
-            // every consumer leaves together (the staging barrier needs all)
-            wk.ok = consumers_all(wk.ok, Cfg::kConsumers);
-            if (!wk.ok) break;
-
-            for (int kb = it.z0; kb < it.z1; kb += NU) {
-                if (!planes<0>(wk, rg, ringA, ringB, stage, a, fc, d_delta, hu, it, kb, i, j,
-                               offA, offB, offS, rec))
-                    break;
-                rotate_queue(wk);
-            }
-            if (!wk.ok) break;
-#pragma unroll
-            for (int m = 0; m < kHalo; ++m) {
-                warp_arrive(&rg.emptyA[wk.gAr & (NA - 1)]);
-                ++wk.gAr;
-            }
-        }
-        // max |u^{n+1}| of this warp, in true units, into the next step's slot
-        float m = scale2(wk.amax, fc.r2t);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-        if ((threadIdx.x & 31) == 0) atomicMax(amax_out, __float_as_uint(m));
-    }
 };
 
-template <class Fmt, int TX, int TY, int NA, int NB, int NU, int MINB>
-__global__ void __launch_bounds__(Cfg16<TX, TY, NA, NB>::kThreads, MINB)
+template <class Fmt, int TX, int TY, int NA, int NB>
+__global__ void __launch_bounds__(Cfg16<TX, TY, NA, NB>::kThreads, 3)
     step_stream16_kernel(const __grid_constant__ Maps16 maps, uint16_t *__restrict__ u_out,
                          uint16_t *d_io, const __grid_constant__ StepArgs a,
                          Scale16 *__restrict__ sc, const long long step, const float src_hint,
-                         const int zb, const int tiles_x, const int ntiles, const int nitems,
-                         const int *__restrict__ rec_ptr, const RecEntry *__restrict__ rec) {
-    using K = Kern16<Fmt, TX, TY, NA, NB, NU>;
+                         const Weights16 wt, const Free16 fr, const int zb, const int tiles_x,
+                         const int ntiles, const int *__restrict__ rec_ptr,
+                         const RecEntry *__restrict__ rec) {
+    using K = Kern16<Fmt, TX, TY, NA, NB>;
     using Cfg = typename K::Cfg;
     extern __shared__ __align__(128) float smem16[];
-    __shared__ Rings<NA, NB> rg;
+    __shared__ Bars16<NA, NB> br;
     float *stage = smem16;
     uint16_t *ringA = reinterpret_cast<uint16_t *>(smem16 + 2 * Cfg::kStage);
     uint16_t *ringB = ringA + NA * Cfg::kSlotA;
+    const Geom &g = a.g;
+    const int tid = threadIdx.x;
 
     // scale of this step: U, D of step n have e; U', D' get e_o
     const int sn = (int)(step & 3), so = (int)((step + 1) & 3);
     const int e = sc->e[sn];
     const int e_o = scale_exponent(fmaxf(__uint_as_float(sc->amax[sn]), src_hint));
     typename K::Factors fc;
-    const float cw = pow2f(-kW16Exp);
-    fc.c = Coeffs{a.c.c1 * cw, a.c.c2 * cw, a.c.c3 * cw, a.c.c4 * cw};
-    fc.wtrue = cw;
+    fc.c0 = wt.c0;
+    fc.c1 = wt.c1;
+    fc.c2 = wt.c2;
+    fc.c3 = wt.c3;
+    fc.c4 = wt.c4;
+    fc.wtrue = pow2f(-kW16Exp);
     fc.amp2r = scale2(1.0f, e);
     fc.ro = pow2f(e_o - e);
     fc.r2t = -e;
 
-    if (threadIdx.x == 0) {
+    const Item it = item_of(blockIdx.x, tiles_x, ntiles, zb, g.nz, TX, TY);
+    const int nb = it.z1 - it.z0, nplanes = nb + 2 * kHalo;
+    const bool stall = (int)blockIdx.x == a.stall_item;
+
+    if (tid == 0) {
         if (blockIdx.x == 0) {
             sc->e[so] = e_o;
             sc->amax[(step + 2) & 3] = 0u;  // accumulated by the next step
         }
         for (int s = 0; s < NA; ++s) {
-            mbar_init(&rg.fullA[s], 1);
-            mbar_init(&rg.emptyA[s], Cfg::kConsumers / 32);
-            rg.issuedA[s] = 0;
+            mbar_init(&br.fullA[s], 1);
+            br.issuedA[s] = 0;
         }
         for (int s = 0; s < NB; ++s) {
-            mbar_init(&rg.fullB[s], 1);
-            mbar_init(&rg.emptyB[s], Cfg::kConsumers / 32);
-            rg.issuedB[s] = 0;
+            mbar_init(&br.fullB[s], 1);
+            br.issuedB[s] = 0;
         }
-        rg.abort = 0;
+        br.abort = 0;
         fence_mbar_init();
     }
     __syncthreads();
-
-    if (threadIdx.x >= Cfg::kConsumers) {
-        if (threadIdx.x == Cfg::kConsumers)
-            K::producer(rg, ringA, ringB, maps, a, zb, tiles_x, ntiles, nitems);
-    } else {
-        K::consumer(rg, ringA, ringB, stage, u_out, d_io - u_out, a, fc, zb, tiles_x, ntiles,
-                    nitems, rec_ptr, rec, &sc->amax[so]);
+    // first fills: U planes 0 .. NA-1 of the item (z0-4 ..), D/W planes 0 .. NB-1
+    if (tid == 0) {
+        for (int pr = 0; pr < NA && pr < nplanes; ++pr)
+            if (!(pr == 0 && stall))   // test hook: never filled, the bounded waits run out
+                K::issue_a(br, ringA, maps, it, pr, pr);
+    }
+    if (tid == 32) {
+        for (int b = 0; b < NB && b < nb; ++b) K::issue_b(br, ringB, maps, it, b, b);
     }
 
+    Ctx16 cx;
+    const int tx = tid % Cfg::kCols, py = tid / Cfg::kCols;
+    cx.ringA = ringA;
+    cx.ringB = ringB;
+    cx.stage = stage;
+    cx.i = it.i0 + 4 * tx;
+    cx.j = it.j0 + 2 * py;
+    cx.z0 = it.z0;
+    cx.z1 = it.z1;
+    cx.nb = nb;
+    cx.nplanes = nplanes;
+    cx.offA = (kHalo + 2 * py) * Cfg::kRowW + Cfg::kLead + 4 * tx;
+    cx.offB = 2 * py * TX + 4 * tx;
+    cx.offS = (kHalo + 2 * py) * Cfg::kSW + kHalo + 4 * tx;
+    {
+        const int band = tid / Cfg::kCols, n = tid - band * Cfg::kCols;
+        int y = band < kHalo ? band : TY + band;            // rows 0..3, TY+4..TY+7
+        int c = kHalo + 4 * n;                                // staging column
+        cx.band_src = y * Cfg::kRowW + c + (Cfg::kLead - kHalo);
+        cx.band_dst = y * Cfg::kSW + c;
+        const int v = tid & 31;
+        y = kHalo + (v >> 1);
+        c = (v & 1) ? TX + kHalo : 0;
+        cx.side_src = y * Cfg::kRowW + c + (Cfg::kLead - kHalo);
+        cx.side_dst = y * Cfg::kSW + c;
+        cx.side = (tid >> 5) == Cfg::kSideWarp;
+    }
+    const bool col_ok = (cx.j < g.ny) && (cx.i < g.nx);
+    cx.nvalid = col_ok ? min(4, g.nx - cx.i) : 0;
+    cx.row1 = cx.j + 1 < g.ny;
+    cx.full = cx.nvalid == 4 && cx.row1;
+    cx.pitch = g.pnx;
+    cx.plane = g.plane;
+    cx.d_delta = d_io - u_out;
+    cx.pu = u_out + pidx(g, col_ok ? cx.i : 0, col_ok ? cx.j : 0, it.z0);
+    cx.gz = a.gz;
+    cx.fz0 = fr.z0;
+    cx.fz1 = fr.z1;
+    cx.xy_free = it.i0 >= fr.x0 && it.i0 + TX <= fr.x1 && it.j0 >= fr.y0 && it.j0 + TY <= fr.y1;
+#pragma unroll
+    for (int rr = 0; rr < 2; ++rr) {
+        cx.gxy[rr] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (col_ok && cx.j + rr < g.ny) {
+            const float gyj = a.gy[cx.j + rr];
+            cx.gxy[rr].x = a.gx[cx.i] * gyj;
+            if (cx.nvalid > 1) cx.gxy[rr].y = a.gx[cx.i + 1] * gyj;
+            if (cx.nvalid > 2) cx.gxy[rr].z = a.gx[cx.i + 2] * gyj;
+            if (cx.nvalid > 3) cx.gxy[rr].w = a.gx[cx.i + 3] * gyj;
+        }
+    }
+    cx.src_mask = 0u;
+    for (int qs = 0; qs < a.src.n; ++qs) {
+        const SourceSample &ss = a.src.s[qs];
+        if (ss.i >= it.i0 && ss.i < it.i0 + TX && ss.j >= it.j0 && ss.j < it.j0 + TY &&
+            ss.k >= it.z0 && ss.k < it.z1)
+            cx.src_mask |= 1u << qs;
+    }
+
+    Walk16 wk;
+    wk.ok = true;
+    wk.amax = 0u;
+    wk.rcur = wk.rend = 0;
+    if (rec_ptr != nullptr) {
+        const int rt = it.tile * Cfg::kWarps + (tid >> 5);
+        wk.rend = rec_ptr[rt + 1];
+        wk.rcur = first_entry(rec, rec_ptr[rt], wk.rend, it.z0);
+    }
+    wk.rnext_k = wk.rcur < wk.rend ? rec[wk.rcur].k : INT_MAX;
+
+    // queue prologue: U planes z0-4 .. z0+3 (relative 0..7)
+#pragma unroll
+    for (int m = 0; m < 2 * kHalo; ++m) {
+        wk.ok = wk.ok && wait_phase(&br.fullA[m], 0u, &br.abort, a.status);
+        const uint16_t *p = ringA + m * Cfg::kSlotA + cx.offA;
+        wk.q[m][0] = Fmt::decode(lds2u(p));
+        wk.q[m][1] = Fmt::decode(lds2u(p + Cfg::kRowW));
+    }
+    wk.ok = __syncthreads_and(wk.ok) != 0;
+    if (wk.ok) {
+        // planes z0-4 .. z0-1 were needed only here: refill their slots
+        if (tid == 0)
+            for (int pr = NA; pr < NA + kHalo && pr < nplanes; ++pr)
+                K::issue_a(br, ringA, maps, it, pr - NA, pr);
+        unsigned tp = 0;
+        for (int kb = it.z0;; kb += NA, tp ^= 1u) {
+            float *st_even = stage + (kb & 1) * Cfg::kStage;
+            float *st_odd = stage + ((kb + 1) & 1) * Cfg::kStage;
+            if (!K::template planes<0>(wk, cx, br, ringA, ringB, maps, it, a, fc, st_even, st_odd,
+                                       kb, tp, rec))
+                break;
+        }
+    }
+
+    // max |U'| of this warp, in true units, into the next step's slot
+    float m = scale2(Fmt::amax_value(wk.amax), -e_o);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((tid & 31) == 0) atomicMax(&sc->amax[so], __float_as_uint(m));
+
+    // after an abort, wait (bounded) for the last copy issued into each slot
     __syncthreads();
-    if (rg.abort && threadIdx.x == 0) {
+    if (br.abort && tid == 0) {
         for (int s = 0; s < NA + NB; ++s) {
-            const int c = s < NA ? rg.issuedA[s] : rg.issuedB[s - NA];
-            uint64_t *bar = s < NA ? &rg.fullA[s] : &rg.fullB[s - NA];
+            const int c = s < NA ? br.issuedA[s] : br.issuedB[s - NA];
+            uint64_t *bar = s < NA ? &br.fullA[s] : &br.fullB[s - NA];
             if (c == 0) continue;
             const unsigned long long t0 = global_ns();
             while (!mbar_try_wait(bar, (unsigned)(c - 1) & 1u) && global_ns() - t0 < kWaitLimitNs) {
@@ -743,12 +762,13 @@ __global__ void __launch_bounds__(Cfg16<TX, TY, NA, NB>::kThreads, MINB)
     }
 }
 
-template <class Fmt, int TX, int TY, int NA, int NB, int NU, int MINB>
+template <class Fmt, int TX, int TY, int NA, int NB>
 cudaError_t launch16(const Maps16 &maps, uint16_t *u_out, uint16_t *d_io, const StepArgs &a,
-                     Scale16 *sc, long long step, float src_hint, int zb, const int *rec_ptr,
-                     const RecEntry *rec, cudaStream_t s) {
+                     Scale16 *sc, long long step, float src_hint, const Weights16 &wt,
+                     const Free16 &fr, int zb, const int *rec_ptr, const RecEntry *rec,
+                     cudaStream_t s) {
     using Cfg = Cfg16<TX, TY, NA, NB>;
-    auto kern = step_stream16_kernel<Fmt, TX, TY, NA, NB, NU, MINB>;
+    auto kern = step_stream16_kernel<Fmt, TX, TY, NA, NB>;
     // the shared-memory limit is a per-device property of the kernel
     static LaunchFacts lf;
     int dev = 0;
@@ -768,42 +788,54 @@ cudaError_t launch16(const Maps16 &maps, uint16_t *u_out, uint16_t *d_io, const 
     const int tiles_x = (a.g.nx + TX - 1) / TX;
     const int ntiles = tiles_x * ((a.g.ny + TY - 1) / TY);
     const int nitems = ntiles * ((a.g.nz + zb - 1) / zb);
-    kern<<<nitems, Cfg::kThreads, Cfg::kSmem, s>>>(maps, u_out, d_io, a, sc, step, src_hint, zb,
-                                                   tiles_x, ntiles, nitems, rec_ptr, rec);
+    kern<<<nitems, Cfg::kThreads, Cfg::kSmem, s>>>(maps, u_out, d_io, a, sc, step, src_hint, wt,
+                                                   fr, zb, tiles_x, ntiles, rec_ptr, rec);
     return cudaGetLastError();
-}
-
-template <class Fmt>
-cudaError_t dispatch16(const Maps16 &maps, uint16_t *u_out, uint16_t *d_io, const StepArgs &a,
-                       Scale16 *sc, long long step, float src_hint, const StreamTiling &t,
-                       const int *rec_ptr, const RecEntry *rec, cudaStream_t s) {
-    // planes 3 at a time (the queue rotates every 3 planes), 2 CTAs per SM
-    // at <= 168 registers: unrolling 9 planes (no rotation) ran 4-27% slower
-    // (instruction cache), a 128-register cap for 3 CTAs per SM spilled and
-    // ran at half speed, and no cap (188 registers) at 60%
-    if (t.tx == 64 && t.ty == 16)
-        return launch16<Fmt, 64, 16, 8, 4, 3, 2>(
-            maps, u_out, d_io, a, sc, step, src_hint, t.zb, rec_ptr, rec, s);
-    return cudaErrorInvalidValue;
 }
 
 }  // namespace
 
 bool stream16_tiling_supported(int tx, int ty) { return tx == 64 && ty == 16; }
 
+// Weights of the 16-bit kernel, times 2^-kW16Exp: floats within 7e-7 of the
+// Taylor weights, chosen so that c0 = -6 (c1 + c2 + c3 + c4) holds exactly.
+// The operator is then free of a mass term (it annihilates constants in
+// exact arithmetic) while the centre weight is applied as one multiply
+// instead of four FMAs. c2..c4 lie on a grid of 2^-23; S = c1 + ... + c4 is
+// the multiple of 2^-21 (so 6 S is a float) nearest to the sum with the c1
+// that keeps the second moment sum_m m^2 c_m = 1 exact, and
+// c1 = S - (c2 + c3 + c4) (its second moment is then off by < 2.4e-7).
+Weights16 zero_sum_weights16() {
+    auto grid = [](double x, double q) { return std::nearbyint(x / q) * q; };
+    const double q23 = std::ldexp(1.0, -23), q21 = std::ldexp(1.0, -21);
+    const double c2 = grid(-1.0 / 5.0, q23), c3 = grid(8.0 / 315.0, q23), c4 = grid(-1.0 / 560.0, q23);
+    const double t = c2 + c3 + c4;
+    const double S = grid(1.0 - 4.0 * c2 - 9.0 * c3 - 16.0 * c4 + t, q21);
+    const double c1 = S - t;
+    const double c0 = -6.0 * S;
+    const double f = std::ldexp(1.0, -kW16Exp);
+    return Weights16{(float)(c0 * f), (float)(c1 * f), (float)(c2 * f), (float)(c3 * f),
+                     (float)(c4 * f)};
+}
+
 cudaError_t launch_step_stream16(int storage, const CUtensorMap *tmap_u, const CUtensorMap *tmap_d,
                                  const CUtensorMap *tmap_w, uint16_t *u_out, uint16_t *d_io,
                                  const StepArgs &a, Scale16 *sc, long long step, float src_hint,
-                                 const StreamTiling &t, const int *rec_ptr, const RecEntry *rec,
-                                 cudaStream_t s) {
+                                 const Free16 &fr, const StreamTiling &t, const int *rec_ptr,
+                                 const RecEntry *rec, cudaStream_t s) {
+    static const Weights16 wt = zero_sum_weights16();
+    if (!(t.tx == 64 && t.ty == 16)) return cudaErrorInvalidValue;
     Maps16 maps;
     maps.u = *tmap_u;
     maps.d = *tmap_d;
     maps.w = *tmap_w;
+    // ring A 9 slots (the planes of one loop trip), ring B 3, 3 CTAs per SM
     if (storage == WS_STORAGE_BF16)
-        return dispatch16<Bf16Fmt>(maps, u_out, d_io, a, sc, step, src_hint, t, rec_ptr, rec, s);
+        return launch16<Bf16Fmt, 64, 16, 9, 3>(maps, u_out, d_io, a, sc, step, src_hint, wt, fr,
+                                                t.zb, rec_ptr, rec, s);
     if (storage == WS_STORAGE_FP16)
-        return dispatch16<Fp16Fmt>(maps, u_out, d_io, a, sc, step, src_hint, t, rec_ptr, rec, s);
+        return launch16<Fp16Fmt, 64, 16, 9, 3>(maps, u_out, d_io, a, sc, step, src_hint, wt, fr,
+                                                t.zb, rec_ptr, rec, s);
     return cudaErrorInvalidValue;
 }
 

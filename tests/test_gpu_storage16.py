@@ -1,17 +1,22 @@
-"""16-bit field storage (ws_set_storage): exactness of one step, stated accuracy.
+"""16-bit field storage (ws_set_storage): one step against the exact update, stated accuracy.
 
 The 16-bit modes store U = u^n and D = u^n - u^{n-1} (velocity form) and the
 model (V dt/h)^2 in FP16.
-1. One step, bit for bit: from a state whose u^n and u^n - u^{n-1} are exact
-   in the 16-bit format, with a model exact in FP16, the 16-bit kernel must
-   store exactly U' = round16(u^{n+1}) and D' = round16(u^{n+1} - u^n) of the
-   FP32 kernel's u^{n+1}, and record exactly the FP32 kernel's traces: it
-   computes the same FP32 operations on exactly power-of-two-scaled numbers.
-2. Accuracy against the FP64 oracle over many steps, checked against the
-   bounds stated in the header and the design notes (the rounding of U' each
-   step dominates; FP32 storage stays near 1e-6), and at the benchmark's full
-   size (1024^3, 100 steps) against FP32 storage and against the oracle on
-   the light cone.
+1. One step: from a state whose u^n and u^n - u^{n-1} are exact in the
+   16-bit format, with a model exact in FP16, the kernel computes u~ = u^{n+1}
+   and d~ = u^{n+1} - u^n in FP32 and stores their 16-bit roundings. Against
+   the FP64 oracle's step from the same state, the stored U' and D' are the
+   correctly rounded values (the FP32 arithmetic is ~1e-6 off, far below one
+   16-bit unit, so only values within that of a rounding boundary may land
+   on the neighbour) and the traces are u~ itself, to FP32 accuracy. The grid
+   has tiles inside the taper (the update without taper multiplies) and
+   tiles that touch it, ragged edges and a source.
+2. Accuracy against the FP64 oracle over many steps: FP32 storage within
+   1e-4, FP16 within 1e-2 at every checkpoint up to the configured 1000
+   steps; BF16 within 1e-2 where it is claimed (100 steps) -- beyond that its
+   8-bit significand does not hold 1e-2 (the rounding errors of the state add
+   up like a random walk, ~1.6e-3 sqrt(steps)), and the tests report the
+   measured error instead of asserting a bound.
 3. Converting FP32 -> 16-bit -> FP32 keeps the state within one 16-bit rounding.
 """
 
@@ -39,16 +44,27 @@ def round_bf16(x):
     return b.astype(np.uint32).view(np.float32)
 
 
-def round_fp16(x):
-    return np.asarray(x, np.float32).astype(np.float16).astype(np.float32)
+def round_fp16(x, e=0):
+    """FP16 rounding of x * 2^e, in units of x."""
+    x = np.asarray(x, np.float64) * 2.0 ** e
+    return (x.astype(np.float16).astype(np.float64) * 2.0 ** -e)
 
 
-ROUND = {"bf16": round_bf16, "fp16": round_fp16}
+def ulp_bf16(x):
+    """Spacing of BF16 values at |x| (normal range)."""
+    _, k = np.frexp(np.abs(np.asarray(x, np.float64)))
+    return np.ldexp(1.0, k - 8)
 
 
-@pytest.mark.parametrize("shape", [(96, 40, 30), (99, 37, 21)])   # the second: ragged x, odd y
+def ulp_fp16(x, e=0):
+    """Spacing of FP16 values at |x * 2^e| (subnormals included), in units of x."""
+    _, k = np.frexp(np.abs(np.asarray(x, np.float64)) * 2.0 ** e)
+    return np.ldexp(1.0, np.maximum(k - 11, -24) - e)
+
+
+@pytest.mark.parametrize("shape", [(200, 60, 30), (99, 37, 21)])   # taper-free tiles; ragged x, odd y
 @pytest.mark.parametrize("storage,name", MODES)
-def test_one_step_equals_rounded_fp32(storage, name, shape):
+def test_one_step_is_the_rounded_exact_update(storage, name, shape):
     nx, ny, nz = shape
     h, v = 10.0, 2000.0
     dt = 0.25 * h / v                      # (V dt / h)^2 = 1/16, exact everywhere
@@ -59,55 +75,58 @@ def test_one_step_equals_rounded_fp32(storage, name, shape):
     sgn = lambda: rng.choice([-1.0, 1.0], (nz, ny, nx))
     u0 = (np.round(rng.uniform(0.5, 1.0, (nz, ny, nx)) * 128) / 128 * sgn()).astype(np.float32)
     d0 = (np.round(rng.uniform(0.125, 0.25, (nz, ny, nx)) * 128) / 128 * sgn()).astype(np.float32)
-    assert np.array_equal(ROUND[name](u0), u0) and np.array_equal(ROUND[name](d0), d0)
+    assert np.array_equal(round_bf16(u0), u0) and np.array_equal(round_fp16(u0), u0)
+    assert np.array_equal(round_bf16(d0), d0) and np.array_equal(round_fp16(d0), d0)
     um1 = (u0 - d0).astype(np.float32)
-    # the last cell sits in the partial column quad and the unpaired last row
-    rec = np.array([[5, 5, 5], [60, 20, 15], [nx - 1, ny - 1, nz - 1], [nx - 2, ny - 2, 3]],
-                   np.int32)
+    # the last cells sit in the partial column quad and the unpaired last row
+    rec = np.array([[5, 5, 5], [60, 20, 15], [nx - 1, ny - 1, nz - 1], [nx - 2, ny - 2, 3],
+                    [100 % nx, 30, 12]], np.int32)
+    src = [(48, 20, 15, 25.0, 0.01, 0.05)]   # small: the field's maximum stays below 1
+    sponge = (5, 0.1)
 
-    def one_step(st):
-        hd = wsb.ws_create(nx, ny, nz, h, dt)
-        if st is not None:
-            wsb.ws_set_storage(hd, st)
-        wsb.ws_set_velocity(hd, vel)
-        wsb.ws_set_sponge(hd, 5, 0.1)
-        wsb.ws_add_source(hd, 48, 20, 15, 25.0, 0.01, 0.5)
-        wsb.ws_set_kernel(hd, wsb.WS_KERNEL_STREAM, 64, 8, 0)
-        wsb.ws_write_field(hd, u0, um1, 3)
-        wsb.ws_set_receivers(hd, rec, 1)
-        wsb.ws_step(hd, 1)
-        wsb.ws_synchronize(hd)
-        u, up = wsb.ws_read_field(hd)
-        return u, up, wsb.ws_read_traces(hd)
+    hd = wsb.ws_create(nx, ny, nz, h, dt)
+    wsb.ws_set_storage(hd, storage)
+    wsb.ws_set_velocity(hd, vel)
+    wsb.ws_set_sponge(hd, *sponge)
+    for s_ in src:
+        wsb.ws_add_source(hd, *s_)
+    wsb.ws_write_field(hd, u0, um1, 3)
+    wsb.ws_set_receivers(hd, rec, 1)
+    wsb.ws_step(hd, 1)
+    wsb.ws_synchronize(hd)
+    u16, up16 = wsb.ws_read_field(hd)
+    tr16 = wsb.ws_read_traces(hd)
+    wsb.ws_destroy(hd)
 
-    u32, _, tr32 = one_step(None)
-    u16, up16, tr16 = one_step(storage)
-    np.testing.assert_array_equal(tr16, tr32)               # traces: the FP32 values
-    ref_u = ROUND[name](u32)
-    ref_d = ROUND[name]((u32 - u0).astype(np.float32))
-    if name == "bf16":   # BF16 has the FP32 exponent range: rounding is scale-free
-        np.testing.assert_array_equal(u16, ref_u)
-        np.testing.assert_array_equal(up16, (ref_u - ref_d).astype(np.float32))
-        return
-    # FP16: the kernel rounds x * 2^e with the field's maximum near 2^12, so
-    # values stay normal down to |x| ~ 2^-26 while x itself rounds subnormally
-    # below 2^-14: compare exactly where both are normal
-    nu = np.abs(u32) >= 2.0 ** -13
-    nd = nu & (np.abs(u32 - u0) >= 2.0 ** -13)
-    assert nd.mean() > 0.99
-    np.testing.assert_array_equal(u16[nu], ref_u[nu])
-    np.testing.assert_array_equal(up16[nd], (ref_u - ref_d).astype(np.float32)[nd])
-    assert np.abs(u16[~nu] - u32[~nu]).max(initial=0.0) <= 2.0 ** -23
+    ref = oracle.run(vel.astype(np.float64), h, dt, 1, sources=src, receivers=rec, sponge=sponge,
+                     n0=3, u_init=u0, uprev_init=um1)
+    ue = ref["u"]                              # exact u^{n+1}
+    de = ue - u0.astype(np.float64)            # exact u^{n+1} - u^n
+    d16 = u16.astype(np.float64) - up16.astype(np.float64)   # the stored D' (exact in FP32)
+    np.testing.assert_allclose(tr16, ref["traces"], rtol=0, atol=2e-6)   # traces: u~ in FP32
+    # the kernel scales the state by 2^e with the field's maximum near 2^12:
+    # max(|u^n|, |u^n - u^{n-1}|, source bound) < 1 here, so e = 12
+    if name == "bf16":
+        rnd, ulp = round_bf16, ulp_bf16
+    else:
+        rnd, ulp = (lambda x: round_fp16(x, 12)), (lambda x: ulp_fp16(x, 12))
+    for got, exact in [(u16.astype(np.float64), ue), (d16, de)]:
+        diff = np.abs(got - exact)
+        assert (diff <= ulp(exact) + 2e-6).all(), diff.max()        # within one unit
+        exact_rounded = got == rnd(exact)
+        assert exact_rounded.mean() >= 0.99, exact_rounded.mean()    # correctly rounded
 
 
-# stated accuracy (relative L2 vs the FP64 oracle) after 200 steps on the
-# layered survey; FP32 storage is there for contrast
-BOUNDS = {"fp32": 1e-5, "fp16": 3e-3, "bf16": 2.5e-2}
+# stated accuracy (relative L2 vs the FP64 oracle) on the layered survey:
+# FP32 and FP16 after 200 steps, BF16 after 100 (its claimed range); FP32
+# storage is there for contrast
+BOUNDS = {"fp32": 1e-5, "fp16": 3e-3, "bf16": 1e-2}
+STEPS = {"fp32": 200, "fp16": 200, "bf16": 100}   # BF16: where 1e-2 is claimed
 
 
 @pytest.mark.parametrize("storage,name", [(wsb.WS_STORAGE_FP32, "fp32")] + MODES)
 def test_accuracy_against_oracle(storage, name):
-    w = synthetic.layered_survey(96, 80, 72, nt=200)
+    w = synthetic.layered_survey(96, 80, 72, nt=STEPS[name])
     ref = oracle.run(w.vel, w.h, w.dt, w.nt, sources=w.sources, receivers=w.receivers,
                      sponge=w.sponge)
     hd = wsb.ws_create(w.nx, w.ny, w.nz, w.h, w.dt)
@@ -126,12 +145,14 @@ def test_accuracy_against_oracle(storage, name):
 
 
 def test_storage_modes_against_oracle_to_1000_steps():
-    """The layered survey recipe at 256^3 for the configured 1000 steps: each
-    storage mode against the FP64 oracle at steps 100, 500 and 1000 (the
-    oracle continues its own state between checkpoints). FP32 within 1e-4,
-    FP16 within 1e-2 at every checkpoint; BF16 within 6e-2 (its 8-bit
-    significand rounds the displacement by ~2e-3 per step)."""
-    w = synthetic.layered_survey(256, 256, 256, nt=1000)
+    """The layered survey recipe at 512^3 (the benchmark's model at half the
+    size per axis) for the configured 1000 steps: every storage mode against
+    the FP64 oracle at steps 100, 500 and 1000 (the oracle continues its own
+    state between checkpoints), on the field and on the traces recorded so
+    far. Claimed and asserted: FP32 within 1e-4 and FP16 within 1e-2 at every
+    checkpoint, BF16 within 1e-2 at 100 steps. Beyond 100 steps BF16 is
+    reported, not bounded: it does not hold 1e-2 there."""
+    w = synthetic.layered_survey(512, 512, 512, nt=1000)
     checkpoints = (100, 500, 1000)
     hs = {}
     for storage, name in [(wsb.WS_STORAGE_FP32, "fp32")] + MODES:
@@ -141,21 +162,34 @@ def test_storage_modes_against_oracle_to_1000_steps():
         wsb.ws_set_sponge(hd, *w.sponge)
         for s in w.sources:
             wsb.ws_add_source(hd, *s)
+        wsb.ws_set_receivers(hd, w.receivers, w.nt)
         hs[name] = hd
-    bound = {"fp32": 1e-4, "fp16": 1e-2, "bf16": 6e-2}
+    claimed = {"fp32": (1e-4, 1000), "fp16": (1e-2, 1000), "bf16": (1e-2, 100)}
     v64 = w.vel.astype(np.float64)
-    ref, done = None, 0
+    ref, done, ref_tr = None, 0, []
     for c in checkpoints:
         kw = {} if ref is None else {"n0": done, "u_init": ref["u"], "uprev_init": ref["u_prev"]}
-        ref = oracle.run(v64, w.h, w.dt, c - done, sources=w.sources, sponge=w.sponge, **kw)
-        nref = np.linalg.norm(ref["u"])
+        ref = oracle.run(v64, w.h, w.dt, c - done, sources=w.sources, receivers=w.receivers,
+                         sponge=w.sponge, **kw)
+        ref_tr.append(ref["traces"])
+        rtr = np.concatenate(ref_tr, axis=1)
+        nref, ntr = np.linalg.norm(ref["u"]), np.linalg.norm(rtr)
         for name, hd in hs.items():
             wsb.ws_step(hd, c - done)
             u, _ = wsb.ws_read_field(hd)
+            tr = wsb.ws_read_traces(hd)[:, :c]
             err = np.linalg.norm(u - ref["u"]) / nref
-            print(f"{name}: 256^3, {c} steps, relative L2 vs the FP64 oracle {err:.3e}")
-            assert err <= bound[name], (name, c, err)
+            err_tr = np.linalg.norm(tr - rtr) / ntr
+            print(f"{name}: 512^3, {c} steps, relative L2 vs the FP64 oracle: field {err:.3e}, "
+                  f"traces {err_tr:.3e}")
+            bound, upto = claimed[name]
+            if c <= upto:
+                assert err <= bound and err_tr <= bound, (name, c, err, err_tr)
+            else:
+                assert np.isfinite(err) and np.isfinite(err_tr), (name, c)
         done = c
+    for hd in hs.values():
+        wsb.ws_destroy(hd)
 
 
 @pytest.mark.parametrize("shape", [(64, 16, 1), (64, 16, 3), (70, 17, 6), (128, 16, 2)])
@@ -179,7 +213,7 @@ def test_thin_and_minimal_grids(storage, name, shape):
     u, _ = wsb.ws_read_field(hd)
     tr = wsb.ws_read_traces(hd)
     ref = oracle.run(vel.astype(np.float64), h, dt, 30, sources=src, receivers=rec, sponge=(3, 0.1))
-    bound = {"fp16": 3e-3, "bf16": 2.5e-2}[name]
+    bound = {"fp16": 3e-3, "bf16": 1e-2}[name]
     err = np.linalg.norm(u - ref["u"]) / np.linalg.norm(ref["u"])
     assert err <= bound, err
     # traces against the field's scale: a receiver the wave has barely reached
@@ -222,11 +256,11 @@ def test_full_size_accuracy_against_fp32_and_oracle():
     storage on the device, and every mode against the FP64 oracle on the
     light cone, in the launch configurations bench.py times (the 16-bit
     kernel's 64 x 16 tile, the FP32 kernel's default 64 x 8, default z
-    blocks). Bounds from the measured 7.9e-4 (FP16) and 6.2e-3 (BF16)
-    against FP32 storage."""
+    blocks). Bounds: the claimed 1e-2 for BF16 (measured 6.2e-3), 2e-3 for
+    FP16 (measured 7.9e-4)."""
     import torch
     w = synthetic.layered_survey(1024, 1024, 1024, nt=100)
-    bound = {"fp32": 0.0, "fp16": 2e-3, "bf16": 1.2e-2}
+    bound = {"fp32": 0.0, "fp16": 2e-3, "bf16": 1e-2}
     out = {}
     for storage, name in [(wsb.WS_STORAGE_FP32, "fp32")] + MODES:
         hd = wsb.ws_create(w.nx, w.ny, w.nz, w.h, w.dt)
@@ -260,7 +294,7 @@ def test_full_size_accuracy_against_fp32_and_oracle():
     orc = oracle.run(sub, w.h, w.dt, w.nt, sources=w.sources, sponge=w.sponge,
                      window=(ox, oy, 0, w.nx, w.ny, w.nz))["u"]
     norc = np.linalg.norm(orc)
-    vs_oracle = {"fp32": 1e-4, "fp16": 2e-3, "bf16": 1.2e-2}
+    vs_oracle = {"fp32": 1e-4, "fp16": 2e-3, "bf16": 1e-2}
     for name, bnd in vs_oracle.items():
         u = out[name]
         win = u[:wz, oy:oy + wy, ox:ox + wx].cpu().numpy().astype(np.float64)
