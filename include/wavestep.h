@@ -180,8 +180,11 @@ int ws_energy(ws_t ws, double *e);
  * there; each call writes every partial it later reads, so nothing needs to
  * start at zero, but calls whose work overlaps on the GPU (other streams,
  * other host threads) race and give wrong results: serialize them.
- * The first call on a device looks up the array's device address (with that
- * device current); make that first call before any stream capture.
+ * Every call looks up the array's address on the current device (the
+ * arrays and the stream must belong to that device), so an address is
+ * never kept across a device reset; the first call on a device may also
+ * load the library's kernels there, so make that first call before any
+ * stream capture.
  * Errors: BADARG, CUDA. */
 #define WS_NOALLOC_MAX_PARTIALS 32768
 int ws_energy_noalloc(const float *u, const float *u_prev, const float *v, int nx, int ny, int nz,

@@ -295,20 +295,34 @@ def ws_energy(ws: Handle) -> float:
 
 
 def ws_energy_noalloc(u, u_prev, v, h: float, dt: float, out, stream=None) -> None:
-    """Energy of device arrays [nz][ny][nx] into the device double out[0]; allocates nothing."""
+    """Energy of device arrays [nz][ny][nx] into the device double out[0]; allocates nothing.
+
+    All four tensors must sit on one CUDA device; the call is made with that
+    device current, on ``stream`` (default: torch's current stream of that
+    device, so the call is ordered after the work that produced the inputs
+    and before the work that reads ``out``). It returns without waiting.
+    """
     import torch
     for t in (u, u_prev, v):
         if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32
                 and t.is_contiguous() and t.dim() == 3 and t.shape == u.shape):
             raise TypeError("u, u_prev, v: contiguous float32 CUDA tensors of one [nz][ny][nx] shape")
-    if not (isinstance(out, torch.Tensor) and out.is_cuda and out.dtype == torch.float64):
+    if not (isinstance(out, torch.Tensor) and out.is_cuda and out.dtype == torch.float64
+            and out.numel() >= 1):
         raise TypeError("out: a float64 CUDA tensor")
+    dev = u.device
+    if any(t.device != dev for t in (u_prev, v, out)):
+        raise TypeError("u, u_prev, v and out must be on one CUDA device")
     nz, ny, nx = u.shape
-    raw = getattr(stream, "cuda_stream", stream)
-    _check(load_library().ws_energy_noalloc(
-        ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(u_prev.data_ptr()),
-        ctypes.c_void_p(v.data_ptr()), nx, ny, nz, float(h), float(dt),
-        ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(raw or None)), "ws_energy_noalloc")
+    with torch.cuda.device(dev):
+        if stream is None:
+            raw = torch.cuda.current_stream(dev).cuda_stream
+        else:
+            raw = getattr(stream, "cuda_stream", stream)
+        _check(load_library().ws_energy_noalloc(
+            ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(u_prev.data_ptr()),
+            ctypes.c_void_p(v.data_ptr()), nx, ny, nz, float(h), float(dt),
+            ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(raw or None)), "ws_energy_noalloc")
 
 
 def ws_autotune(ws: Handle):

@@ -98,8 +98,8 @@ __global__ void velocity_to_w_kernel(float *__restrict__ w, Geom g, double dt_ov
         } else {
             vmin = 0u;
         }
-        const double r = (double)v * dt_over_h;
-        w[p] = (float)(r * r);
+        const double r = __dmul_rn((double)v, dt_over_h);   // as ws_energy_noalloc forms it
+        w[p] = (float)__dmul_rn(r, r);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {

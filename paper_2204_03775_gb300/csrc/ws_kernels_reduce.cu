@@ -9,8 +9,6 @@
 // the float fields: each block sums a fixed set of rows into one partial,
 // and one block adds the partials in a fixed order, so the result does not
 // depend on scheduling.
-#include <mutex>
-
 #include "ws_internal.h"
 
 namespace ws {
@@ -46,8 +44,8 @@ struct DenseFields {
         return in ? p[at(i, j, k)] : 0.0f;
     }
     __device__ float w_at(int i, int j, int k) const {
-        const double r = (double)v[at(i, j, k)] * dt_over_h;
-        return (float)(r * r);
+        const double r = __dmul_rn((double)v[at(i, j, k)], dt_over_h);
+        return (float)__dmul_rn(r, r);
     }
 };
 
@@ -63,20 +61,22 @@ __global__ void __launch_bounds__(kThreads) energy_partials_kernel(F f, int nx, 
     double acc = 0.0;
     for (int j = j0; j < j1; ++j) {
         for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+            // every operation explicitly rounded (no contraction left to the
+            // compiler), so each field layout gives the same bits
             const double pc = f.p_at(i, j, k);
-            double lx = c.c0 * pc, ly = c.c0 * pc, lz = c.c0 * pc;
+            double lx = __dmul_rn(c.c0, pc), ly = lx, lz = lx;
 #pragma unroll
             for (int m = 1; m <= 4; ++m) {
                 const double cm = m == 1 ? c.c1 : m == 2 ? c.c2 : m == 3 ? c.c3 : c.c4;
-                lx += cm * ((double)f.p_at(i + m, j, k) + (double)f.p_at(i - m, j, k));
-                ly += cm * ((double)f.p_at(i, j + m, k) + (double)f.p_at(i, j - m, k));
-                lz += cm * ((double)f.p_at(i, j, k + m) + (double)f.p_at(i, j, k - m));
+                lx = __fma_rn(cm, __dadd_rn(f.p_at(i + m, j, k), f.p_at(i - m, j, k)), lx);
+                ly = __fma_rn(cm, __dadd_rn(f.p_at(i, j + m, k), f.p_at(i, j - m, k)), ly);
+                lz = __fma_rn(cm, __dadd_rn(f.p_at(i, j, k + m), f.p_at(i, j, k - m)), lz);
             }
-            const double lap = (lx + ly + lz) / h2;
+            const double lap = __ddiv_rn(__dadd_rn(__dadd_rn(lx, ly), lz), h2);
             const double uc = f.u_at(i, j, k);
-            const double d = uc - pc;
-            const double vdt2 = (double)f.w_at(i, j, k) * h2;   // (V dt)^2
-            acc += d * d / vdt2 - uc * lap;
+            const double d = __dsub_rn(uc, pc);
+            const double vdt2 = __dmul_rn((double)f.w_at(i, j, k), h2);   // (V dt)^2
+            acc = __dadd_rn(acc, __fma_rn(-uc, lap, __ddiv_rn(__dmul_rn(d, d), vdt2)));
         }
     }
     // fixed-order block reduction: warp shuffles, then warp 0
@@ -143,25 +143,13 @@ cudaError_t launch_energy_noalloc(const float *u, const float *p, const float *v
                                   int nz, double h, double dt, const Coeffs64 &c, double *out,
                                   cudaStream_t s) {
     // Host code cannot pass g_noalloc_partials itself (in host code the name
-    // is a stand-in, not a device address): look its address up once per
-    // device, with that device current.
-    static std::mutex mu;
-    static double *addr[kNoAllocMaxDevices] = {};
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    // is a stand-in, not a device address): look its address up on the
+    // current device. This is done on every call, so an address never
+    // outlives the context it belongs to (a device reset may move it).
+    void *ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_partials);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kNoAllocMaxDevices) return cudaErrorInvalidDevice;
-    double *partials;
-    {
-        std::lock_guard<std::mutex> lock(mu);
-        if (addr[dev] == nullptr) {
-            void *ptr = nullptr;
-            e = cudaGetSymbolAddress(&ptr, g_noalloc_partials);
-            if (e != cudaSuccess) return e;
-            addr[dev] = static_cast<double *>(ptr);
-        }
-        partials = addr[dev];
-    }
+    double *partials = static_cast<double *>(ptr);
     DenseFields f{u, p, v, nx, ny, nz, dt / h};
     return launch_energy(f, nx, ny, nz, h, c, partials, out, s);
 }
