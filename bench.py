@@ -62,6 +62,8 @@ def parse_args():
                     help="skip the 256^3 16-shot adjoint-gradient report")
     ap.add_argument("--no-storage16", action="store_true",
                     help="skip the BF16/FP16 storage timings and errors")
+    ap.add_argument("--no-accuracy", action="store_true",
+                    help="skip the 256^3 accuracy report against the FP64 oracle")
     return ap.parse_args()
 
 
@@ -100,17 +102,66 @@ def measured_peak():
 
 
 class ClockSampler:
-    """nvidia-smi sampling of SM clocks and throttle reasons while it runs."""
+    """SM clocks and throttle reasons sampled while it runs (reads only).
+
+    Primary: NVML through ctypes, polled every few milliseconds from a thread,
+    so that even a timed region well under a second gets many samples.
+    Fallback: nvidia-smi at its 200 ms loop."""
 
     FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw",
               "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
               "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+    # NVML clock event reason bits
+    REASONS = {0x8: "hw_slowdown", 0x40: "hw_thermal_slowdown", 0x20: "sw_thermal_slowdown",
+               0x4: "sw_power_cap"}
 
-    def __init__(self, gpu_id):
+    def __init__(self, gpu_id, period_s=0.005):
         self.proc = None
         self.gpu_id = gpu_id
+        self.period_s = period_s
+        self.rows = []
+        self.source = None
+        self._stop = None
+        self._thread = None
+
+    def _nvml_open(self):
+        import ctypes
+        lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if lib.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit failed")
+        handle = ctypes.c_void_p()
+        if self.gpu_id:
+            rc = lib.nvmlDeviceGetHandleByUUID(self.gpu_id.encode(), ctypes.byref(handle))
+        else:
+            rc = lib.nvmlDeviceGetHandleByIndex_v2(0, ctypes.byref(handle))
+        if rc != 0:
+            raise OSError(f"nvmlDeviceGetHandle: {rc}")
+        return lib, handle
+
+    def _poll(self, lib, handle):
+        import ctypes
+        mhz, mx, why = ctypes.c_uint(), ctypes.c_uint(), ctypes.c_ulonglong()
+        get_reasons = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        lib.nvmlDeviceGetMaxClockInfo(handle, 1, ctypes.byref(mx))
+        while not self._stop.is_set():
+            if (lib.nvmlDeviceGetClockInfo(handle, 1, ctypes.byref(mhz)) == 0
+                    and get_reasons(handle, ctypes.byref(why)) == 0):
+                names = [n for bit, n in self.REASONS.items() if why.value & bit]
+                self.rows.append((float(mhz.value), float(mx.value), names))
+            self._stop.wait(self.period_s)
 
     def __enter__(self):
+        import threading
+        try:
+            lib, handle = self._nvml_open()
+            self._stop = threading.Event()
+            self._thread = threading.Thread(target=self._poll, args=(lib, handle), daemon=True)
+            self._thread.start()
+            self.source = "nvml"
+            return self
+        except (OSError, AttributeError):
+            pass
         cmd = ["nvidia-smi", f"--query-gpu={','.join(self.FIELDS)}",
                "--format=csv,noheader,nounits", "-lms", "200"]
         if self.gpu_id:
@@ -118,11 +169,15 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
                                          text=True)
+            self.source = "nvidia-smi"
         except OSError:
             self.proc = None
         return self
 
     def __exit__(self, *exc):
+        if self._thread is not None:
+            self._stop.set()
+            self._thread.join(timeout=5)
         if self.proc is not None:
             self.proc.terminate()
             try:
@@ -130,26 +185,24 @@ class ClockSampler:
             except subprocess.TimeoutExpired:
                 self.proc.kill()
                 self.out, _ = self.proc.communicate()
+            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+            for line in (self.out or "").splitlines():
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) != len(self.FIELDS):
+                    continue
+                try:
+                    flags = [names[i] for i, f in enumerate(parts[3:]) if f.lower() == "active"]
+                    self.rows.append((float(parts[0]), float(parts[1]), flags))
+                except ValueError:
+                    continue
 
     def summary(self):
-        if self.proc is None:
+        if not self.rows:
             return None
-        rows = []
-        for line in (self.out or "").splitlines():
-            parts = [p.strip() for p in line.split(",")]
-            if len(parts) != len(self.FIELDS):
-                continue
-            try:
-                rows.append((float(parts[0]), float(parts[1]), parts[3:]))
-            except ValueError:
-                continue
-        if not rows:
-            return None
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for _, _, flags in rows for i, f in enumerate(flags)
-                          if f.lower() == "active"})
-        return {"sm_mhz": statistics.median(r[0] for r in rows),
-                "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons, "samples": len(rows)}
+        reasons = sorted({n for _, _, flags in self.rows for n in flags})
+        return {"sm_mhz": statistics.median(r[0] for r in self.rows),
+                "sm_max_mhz": max(r[1] for r in self.rows), "reasons": reasons,
+                "samples": len(self.rows), "source": self.source}
 
 
 def dist_setup(n_gpus):
@@ -263,9 +316,66 @@ def storage16_report(w, K, W, stream, peak):
         done = c
     for name, _ in modes:
         out[name]["rel_l2_vs_fp32_at_steps"] = dict(zip(map(str, checkpoints), errs[name]))
+        out[name]["limits"] = ("single grids with nx >= 64 and ny >= 16; batches and the "
+                               "adjoint gradient run FP32 storage")
     for h in hs.values():
         wsb.ws_destroy(h)
     return out
+
+
+def accuracy_report(n=256, checkpoints=(100, 500, 1000)):
+    """Every storage mode against the FP64 oracle on the layered survey at
+    n^3 (the oracle runs on the host cores: ~30 s at 256^3 on 16 cores; the
+    1024^3 field would need ~26 GB and half an hour), relative L2 of the
+    field and of the traces recorded so far, at each checkpoint."""
+    import numpy as np
+    import oracle
+    import paper_2204_03775_gb300 as wsb
+    from paper_2204_03775_gb300 import synthetic
+
+    oracle.build()
+    w = synthetic.layered_survey(n, n, n, nt=checkpoints[-1])
+    modes = [("fp32", wsb.WS_STORAGE_FP32), ("fp16", wsb.WS_STORAGE_FP16),
+             ("bf16", wsb.WS_STORAGE_BF16)]
+    hs = {}
+    for name, st in modes:
+        h = wsb.ws_create(w.nx, w.ny, w.nz, w.h, w.dt)
+        wsb.ws_set_storage(h, st)
+        wsb.ws_set_velocity(h, w.vel)
+        wsb.ws_set_sponge(h, *w.sponge)
+        for s in w.sources:
+            wsb.ws_add_source(h, *s)
+        wsb.ws_set_receivers(h, w.receivers, w.nt)
+        hs[name] = h
+    out = {name: {"field": {}, "traces": {}} for name, _ in modes}
+    v64 = w.vel.astype(np.float64)
+    ref, done, ref_tr = None, 0, []
+    t0 = time.perf_counter()
+    for c in checkpoints:
+        kw = {} if ref is None else {"n0": done, "u_init": ref["u"], "uprev_init": ref["u_prev"]}
+        ref = oracle.run(v64, w.h, w.dt, c - done, sources=w.sources, receivers=w.receivers,
+                         sponge=w.sponge, **kw)
+        ref_tr.append(ref["traces"])
+        rtr = np.concatenate(ref_tr, axis=1)
+        nref, ntr = np.linalg.norm(ref["u"]), np.linalg.norm(rtr)
+        for name, h in hs.items():
+            wsb.ws_step(h, c - done)
+            u, _ = wsb.ws_read_field(h)
+            tr = wsb.ws_read_traces(h)[:, :c]
+            out[name]["field"][str(c)] = float(np.linalg.norm(u - ref["u"]) / nref)
+            out[name]["traces"][str(c)] = float(np.linalg.norm(tr - rtr) / ntr)
+        done = c
+    for h in hs.values():
+        wsb.ws_destroy(h)
+    bound = {"fp32": 1e-4, "fp16": 1e-2, "bf16": 1e-2}
+    for name, _ in modes:
+        errs = list(out[name]["field"].values()) + list(out[name]["traces"].values())
+        out[name]["bound"] = bound[name]
+        out[name]["within_bound_at_every_checkpoint"] = bool(max(errs) <= bound[name])
+    return {"workload": f"layered_survey {n}x{n}x{n} (the benchmark's model recipe), "
+                        f"{checkpoints[-1]} steps, FP64 oracle on {oracle.num_threads()} host "
+                        f"cores ({time.perf_counter() - t0:.0f} s)",
+            "metric": "relative L2 vs the FP64 oracle", **out}
 
 
 def _shot_handle(wsb, w, nt_max):
@@ -353,14 +463,17 @@ def adjoint_report():
     dev = torch.device("cuda")
     m_true = torch.from_numpy((1.0 / w.vel_true.astype(np.float64) ** 2).astype(np.float32)).to(dev)
     m0 = torch.from_numpy((1.0 / w.vel_start.astype(np.float64) ** 2).astype(np.float32)).to(dev)
-    hs = []
+    hs, streams = [], []
     for shot in w.shots:
         h = wsb.ws_create(w.nx, w.ny, w.nz, w.h, w.dt)
+        st = torch.cuda.Stream()       # one stream per shot: the shots' kernels overlap
+        wsb.ws_set_stream(h, st)
         wsb.ws_set_sponge(h, *w.sponge)
         for s in shot:
             wsb.ws_add_source(h, *s)
         wsb.ws_set_receivers(h, w.receivers, w.nt)
         hs.append(h)
+        streams.append(st)
     for h in hs:
         wsb.ws_set_slowness2(h, m0)
         tiling = wsb.ws_autotune(h)     # timed once, then cached for the grid size
@@ -386,19 +499,26 @@ def adjoint_report():
     fwd_s = time.perf_counter() - t0
     g = torch.zeros_like(m0)
     gs = torch.empty_like(m0)
+    for h in hs:
+        wsb.ws_set_slowness2(h, m0)
+    # the 16 shots in one call (each on its own stream, interleaved step by step)
     times = []
     for rep in range(2):
-        g.zero_()
-        J = 0.0
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for h, d in zip(hs, d_obs):
-            wsb.ws_set_slowness2(h, m0)
-            _, j = wsb.ws_adjoint_gradient(h, d, wsb.WS_ADJ_DATA, gs)
-            g += gs
-            J += j
+        g, J, gnorm = wsb.ws_adjoint_gradient_shots(hs, d_obs, wsb.WS_ADJ_DATA, g)
         torch.cuda.synchronize()
         times.append(time.perf_counter() - t0)
+    # the same shots one call at a time, for contrast
+    g_seq = torch.zeros_like(m0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for h, d in zip(hs, d_obs):
+        _, j = wsb.ws_adjoint_gradient(h, d, wsb.WS_ADJ_DATA, gs)
+        g_seq += gs
+    torch.cuda.synchronize()
+    seq_s = time.perf_counter() - t0
+    seq_rel = float((g_seq - g).abs().max() / g.abs().max())
     for h in hs:
         wsb.ws_destroy(h)
     del hs
@@ -426,7 +546,11 @@ def adjoint_report():
             "gradient_s": min(times), "forward_s": fwd_s,
             "gradient_over_forward": min(times) / fwd_s,
             "forward_rate": {"value": len(w.shots) * cells * w.nt / fwd_s / 1e9, "unit": UNIT},
-            "misfit": J, "grad_max_abs": float(g.abs().max()),
+            "misfit": J, "grad_max_abs": float(g.abs().max()), "grad_norm_fp64": gnorm,
+            "how": "ws_adjoint_gradient_shots: the 16 shots in one call, each on its own "
+                   "stream, interleaved step by step",
+            "sequential": {"gradient_s": seq_s, "max_rel_diff": seq_rel,
+                           "what": "the same 16 shots, one ws_adjoint_gradient call each"},
             "tiling": {"tile": f"{tiling[0]}x{tiling[1]}", "zblock": tiling[2]},
             "passes": "forward (traces + sqrt(N) checkpoints), residual, then per segment a "
                       "recomputation and the adjoint steps with injection and imaging",
@@ -434,7 +558,7 @@ def adjoint_report():
                                "grad_vs_ws_adjoint_gradient": auto_rel,
                                "what": "loss = sum over shots of 0.5 |traces(m) - d|^2; "
                                        "loss.backward() (ws_forward + residual-mode adjoint)"},
-            "timing": "host clock, 16 shots one after another"}
+            "timing": "host clock"}
 
 
 def run_case(args):
@@ -450,6 +574,8 @@ def run_case(args):
     if args.case in ("fp16", "bf16"):
         w = synthetic.layered_survey(n, n, n, nt=K + W)
         h = wsb.ws_create(w.nx, w.ny, w.nz, w.h, w.dt)
+        tx, ty = (int(x) for x in args.tile.split("x"))
+        wsb.ws_set_kernel(h, wsb.WS_KERNEL_AUTO, tx, ty, args.zblock)
         wsb.ws_set_storage(h, wsb.WS_STORAGE_FP16 if args.case == "fp16" else wsb.WS_STORAGE_BF16)
         wsb.ws_set_velocity(h, w.vel)
         wsb.ws_set_sponge(h, *w.sponge)
@@ -658,6 +784,13 @@ def main():
         line["storage16"] = storage16_report(w, K, W, stream, peak)
         for mode in line["storage16"].values():     # speed relative to FP32 storage
             mode["vs_fp32_storage"] = mode["value"] / line["value"]
+    if world == 1 and not args.no_accuracy:
+        line["accuracy_vs_oracle"] = accuracy_report()
+        if "storage16" in line:
+            for name, mode in line["storage16"].items():
+                mode["rel_l2_vs_oracle_at_steps"] = line["accuracy_vs_oracle"][name]["field"]
+                mode["within_1e-2_vs_oracle"] = \
+                    line["accuracy_vs_oracle"][name]["within_bound_at_every_checkpoint"]
     if world == 1 and not args.no_batched:
         line["batched"] = batched_report(peak)
     if world == 1 and not args.no_adjoint:

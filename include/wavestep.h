@@ -64,6 +64,7 @@ extern "C" {
 #define WS_STORAGE_FP16   2  /* float16 u, u - u_prev; FP16 model: 10 bytes per cell update */
 
 #define WS_MAX_SOURCES   16
+#define WS_MAX_SHOTS     64  /* handles in one ws_adjoint_gradient_shots call */
 
 /* What ws_adjoint_gradient's data array holds. */
 #define WS_ADJ_DATA       0  /* observed traces d: residual = traces - d */
@@ -230,6 +231,27 @@ int ws_energy_noalloc(const float *u, const float *u_prev, const float *v, int n
  * TIMEOUT. */
 int ws_adjoint_gradient(ws_t ws, const float *data, int mode, float *grad_m, double *misfit,
                         int on_device);
+
+/* The gradient of the summed misfit of several shots: nshots handles (1 to
+ * WS_MAX_SHOTS) on grids of one size, with the same nt_max, each with its own
+ * sources, receivers and model (normally one model: the gradient is then
+ * the gradient of the total misfit). data[s] is shot s's data, as for
+ * ws_adjoint_gradient with the same mode. grad_m receives the sum over the
+ * shots of their dJ_s/dm (FP64 sum in shot order, rounded once), *misfit
+ * (may be NULL) the summed misfit, *grad_norm (may be NULL) the FP64 L2
+ * norm of grad_m computed on the device (fixed summation order). Host
+ * (on_device = 0) or device (1) arrays, as in ws_adjoint_gradient.
+ *
+ * Each shot is the computation of ws_adjoint_gradient (the same kernels and
+ * values: one shot's gradient equals that call's bit for bit), issued on its
+ * handle's stream, the shots interleaved step by step: shots on distinct
+ * streams (ws_set_stream) run concurrently and fill the GPU that one small
+ * grid leaves partly idle. The paper has no counterpart (forward problem
+ * only). Synchronizes every shot's stream. Errors: BADARG (sizes or steps
+ * differ, a NULL handle or array, a handle given twice), STATE, OOM, CUDA,
+ * TIMEOUT; with an error the shots' states are unspecified. */
+int ws_adjoint_gradient_shots(ws_t *shots, int nshots, const float *const *data, int mode,
+                              float *grad_m, double *misfit, double *grad_norm, int on_device);
 
 /* The forward run of ws_adjoint_gradient on its own: fields zeroed, step 0,
  * nt_max steps with the handle's sources, traces recorded (ws_read_traces),

@@ -11,7 +11,8 @@ from .binding import (  # noqa: F401
     WS_ADJ_DATA, WS_ADJ_RESIDUAL, WS_ERR_BADARG, WS_ERR_CFL, WS_ERR_CUDA, WS_ERR_OOM, WS_ERR_STATE, WS_ERR_TIMEOUT,
     WS_KERNEL_AUTO, WS_KERNEL_DIRECT, WS_KERNEL_STREAM, WS_MAX_SOURCES, WS_OK, WS_STORAGE_BF16,
     WS_STORAGE_FP16, WS_STORAGE_FP32, Batch, Handle,
-    WaveStepError, load_library, ws_add_source, ws_adjoint_gradient, ws_autotune,
+    WaveStepError, load_library, ws_add_source, ws_adjoint_gradient, ws_adjoint_gradient_shots,
+    ws_autotune,
     ws_batch_create, ws_batch_destroy, ws_batch_get_tiling, ws_batch_launch_count,
     ws_batch_set_tiling, ws_batch_step, ws_batch_synchronize, ws_clear_sources, ws_create, ws_destroy, ws_energy, ws_forward,
     ws_energy_noalloc,

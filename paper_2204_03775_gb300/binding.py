@@ -72,6 +72,8 @@ def load_library(build_if_missing: bool = False):
         "ws_set_slowness2": (i, [vp, vp, i]),
         "ws_adjoint_gradient": (i, [vp, vp, i, vp, ctypes.POINTER(d), i]),
         "ws_forward": (i, [vp]),
+        "ws_adjoint_gradient_shots": (i, [ctypes.POINTER(vp), i, ctypes.POINTER(vp), i, vp,
+                                          ctypes.POINTER(d), ctypes.POINTER(d), i]),
         "ws_set_sponge": (i, [vp, i, d]),
         "ws_add_source": (i, [vp, i, i, i, d, d, d]),
         "ws_clear_sources": (i, [vp]),
@@ -205,6 +207,37 @@ def ws_adjoint_gradient(ws: Handle, data, mode: int = WS_ADJ_DATA, grad_m=None):
                                               ctypes.c_void_p(pg), ctypes.byref(j), dd),
            "ws_adjoint_gradient")
     return grad_m, j.value
+
+
+def ws_adjoint_gradient_shots(shots, data, mode: int = WS_ADJ_DATA, grad_m=None):
+    """(sum of dJ_s/dm [nz][ny][nx], summed J, FP64 ||gradient||_2) of several
+    shots on grids of one size; data: one [nrec_s][nt_max] float32 array per
+    shot, all host or all device arrays (grad_m alike)."""
+    shots = list(shots)
+    data = list(data)
+    if len(shots) != len(data) or not shots:
+        raise ValueError("one data array per shot, at least one shot")
+    ptrs, devs = zip(*(_ptr(d, (h.nrec, h.nt_max)) for h, d in zip(shots, data)))
+    if len(set(devs)) != 1:
+        raise ValueError("data arrays must all be host or all be device arrays")
+    dd = devs[0]
+    if grad_m is None:
+        if dd:
+            import torch
+            grad_m = torch.empty(shots[0].shape, dtype=torch.float32, device=data[0].device)
+        else:
+            grad_m = np.empty(shots[0].shape, np.float32)
+    pg, dg = _ptr(grad_m, shots[0].shape)
+    if dd != dg:
+        raise ValueError("data and grad_m must both be host or both be device arrays")
+    hs = (ctypes.c_void_p * len(shots))(*(h.ptr.value for h in shots))
+    ds = (ctypes.c_void_p * len(shots))(*ptrs)
+    j, gn = ctypes.c_double(), ctypes.c_double()
+    _check(load_library().ws_adjoint_gradient_shots(hs, len(shots), ds, int(mode),
+                                                    ctypes.c_void_p(pg), ctypes.byref(j),
+                                                    ctypes.byref(gn), dd),
+           "ws_adjoint_gradient_shots")
+    return grad_m, j.value, gn.value
 
 
 def ws_forward(ws: Handle) -> None:

@@ -255,14 +255,35 @@ int upload_profiles(ws_t ws) {
     return WS_OK;
 }
 
-int encode_maps16(ws_t ws) {
+int encode_maps16(ws_t ws, int ty) {
     const ws::Geom &g = ws->g;
     int rc = WS_OK;
     for (int b = 0; b < 2 && rc == WS_OK; ++b)
-        rc = encode_map(&ws->t16_halo[b], ws->buf16[b], g, kTile16X + 16, kTile16Y + 2 * ws::kHalo, 2);
-    if (rc == WS_OK) rc = encode_map(&ws->t16_d, ws->d16, g, kTile16X, kTile16Y, 2);
-    if (rc == WS_OK) rc = encode_map(&ws->t16_w, ws->w16, g, kTile16X, kTile16Y, 2);
+        rc = encode_map(&ws->t16_halo[b], ws->buf16[b], g, kTile16X + 16, ty + 2 * ws::kHalo, 2);
+    if (rc == WS_OK) rc = encode_map(&ws->t16_d, ws->d16, g, kTile16X, ty, 2);
+    if (rc == WS_OK) rc = encode_map(&ws->t16_w, ws->w16, g, kTile16X, ty, 2);
+    ws->t16_ty = rc == WS_OK ? ty : 0;
     return rc;
+}
+
+// The 16-bit kernel's tile height for this grid: the one ws_set_kernel chose
+// if the grid holds it, else the first of kTile16Ys that the grid holds.
+int pick_tile16(const ws_t ws) {
+    if (ws->tile16_y > 0 && ws->g.ny >= ws->tile16_y) return ws->tile16_y;
+    for (int ty : kTile16Ys)
+        if (ws->g.ny >= ty) return ty;
+    return 0;
+}
+
+// Planes per work item of the 16-bit kernel: the FP32 kernel's default,
+// shortened on small grids to about two full waves of the resident CTAs.
+int default_zblock16(const ws::Geom &g, int ty) {
+    int zb = default_zblock(g.nz), slots = 0;
+    if (ws::stream16_slots(ty, &slots) != cudaSuccess) return zb;
+    const long long tiles = (long long)((g.nx + kTile16X - 1) / kTile16X) * ((g.ny + ty - 1) / ty);
+    const long long blocks = std::max<long long>(1, 2LL * slots / tiles);
+    const int zs = (int)std::max<long long>(8, (g.nz + blocks - 1) / blocks);
+    return std::min(zb, std::min(zs, g.nz));
 }
 
 // FP32 buffers -> the 16-bit state (U = u^n, D = u^n - u^{n-1}), exponents
@@ -653,10 +674,10 @@ int ws_set_storage(ws_t ws, int storage) {
         return fail(WS_ERR_BADARG, "ws_set_storage: unknown storage %d", storage);
     if (storage == ws->storage) return WS_OK;
     ws->model_version++;
-    if (storage != WS_STORAGE_FP32 && (ws->g.nx < kTile16X || ws->g.ny < kTile16Y))
+    if (storage != WS_STORAGE_FP32 && (ws->g.nx < kTile16X || pick_tile16(ws) == 0))
         return fail(WS_ERR_BADARG,
                     "ws_set_storage: 16-bit storage needs nx >= %d and ny >= %d (grid %d x %d)",
-                    kTile16X, kTile16Y, ws->g.nx, ws->g.ny);
+                    kTile16X, kTile16Ys[kNumTile16Ys - 1], ws->g.nx, ws->g.ny);
     // bring the state to FP32 first
     if (ws->storage != WS_STORAGE_FP32) {
         int rc = decode_state16(ws);
@@ -674,7 +695,7 @@ int ws_set_storage(ws_t ws, int storage) {
             WS_CUDA(cudaMalloc(&ws->scale, sizeof(ws::Scale16)), "cudaMalloc scales");
             WS_CUDA(cudaMemsetAsync(ws->scale, 0, sizeof(ws::Scale16), ws->stream), "zero scales");
         }
-        int rc = encode_maps16(ws);
+        int rc = encode_maps16(ws, pick_tile16(ws));
         if (rc != WS_OK) return rc;
         ws->storage = storage;
         rc = encode_state16(ws);
@@ -692,10 +713,21 @@ int ws_set_kernel(ws_t ws, int kernel, int tile_x, int tile_y, int zblock) {
     if (zblock < 0) return fail(WS_ERR_BADARG, "ws_set_kernel: zblock must be >= 0");
     ws::StreamTiling t = ws->tiling;
     if (tile_x != 0 || tile_y != 0) {
-        if (!ws::stream_tiling_supported(tile_x, tile_y))
+        const bool fp32 = ws::stream_tiling_supported(tile_x, tile_y);
+        const bool t16 = ws::stream16_tiling_supported(tile_x, tile_y);
+        if (!fp32 && !t16)
             return fail(WS_ERR_BADARG, "ws_set_kernel: unsupported tile %d x %d", tile_x, tile_y);
-        t.tx = tile_x;
-        t.ty = tile_y;
+        if (t16) {   // the 16-bit kernel's tile; the FP32 tile only if that kernel has it too
+            if (ws->g.nx < tile_x || ws->g.ny < tile_y)
+                return fail(WS_ERR_BADARG,
+                            "ws_set_kernel: grid %d x %d is smaller than the tile %d x %d",
+                            ws->g.nx, ws->g.ny, tile_x, tile_y);
+            ws->tile16_y = tile_y;
+        }
+        if (fp32) {
+            t.tx = tile_x;
+            t.ty = tile_y;
+        }
     }
     t.zb = zblock;
     if (kernel == WS_KERNEL_STREAM && !stream_fits(ws, t))
@@ -724,8 +756,12 @@ int ws_step(ws_t ws, int nsteps) {
     int kern = WS_KERNEL_STREAM;
     if (ws->storage != WS_STORAGE_FP32) {
         tiling.tx = kTile16X;
-        tiling.ty = kTile16Y;
-        tiling.zb = ws->tiling.zb > 0 ? ws->tiling.zb : default_zblock(ws->g.nz);
+        tiling.ty = pick_tile16(ws);
+        tiling.zb = ws->tiling.zb > 0 ? ws->tiling.zb : default_zblock16(ws->g, tiling.ty);
+        if (tiling.ty != ws->t16_ty) {
+            int rc = encode_maps16(ws, tiling.ty);
+            if (rc != WS_OK) return rc;
+        }
         int rc = build_rec_tiles(ws, tiling, kRows16);
         if (rc != WS_OK) return rc;
         if (!ws->w16_ok) {
@@ -747,10 +783,10 @@ int ws_step(ws_t ws, int nsteps) {
                 hint = std::max(hint, std::fabs((double)a.src.s[q].amp) * ws->wmax);
             a.stall_item = ws->stall_item;
             ws->stall_item = -1;
+            const ws::Maps16In maps{&ws->t16_halo[ws->cur], &ws->t16_d, &ws->t16_w,
+                                    ws->buf16[1 - ws->cur], ws->d16};
             cudaError_t e = ws::launch_step_stream16(
-                ws->storage, &ws->t16_halo[ws->cur], &ws->t16_d, &ws->t16_w,
-                ws->buf16[1 - ws->cur], ws->d16, a, ws->scale, ws->step, (float)hint, ws->free16,
-                tiling,
+                ws->storage, maps, a, ws->scale, ws->step, (float)hint, ws->free16, tiling,
                 ws->nrec > 0 ? ws->rec_ptr : nullptr, ws->rec_entries, ws->stream);
             a.stall_item = -1;
             ws->launches++;

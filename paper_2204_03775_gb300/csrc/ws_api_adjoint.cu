@@ -77,6 +77,7 @@ int adjoint_prepare(ws_t ws, const char *who, int *kern_out, ws::StreamTiling *t
             if (r3 == WS_OK) r3 = field(&f);
         if (r3 == WS_OK) e = grab(&ac->acc, 2 * fb);   // float2 per cell, padded layout
         if (r3 == WS_OK && e == cudaSuccess) e = grab(&ac->partials, sizeof(double) * (ws::residual_partial_count() + 1));
+        if (r3 == WS_OK && e == cudaSuccess) e = grab(&ac->norm, sizeof(double) * (ws::residual_partial_count() + 1));
         if (r3 == WS_OK && e == cudaSuccess) e = grab(&ac->r, sizeof(float) * ntr);
         if (r3 == WS_OK && e == cudaSuccess) e = grab(&ac->dd, sizeof(float) * ntr);
         if (r3 == WS_OK && e == cudaSuccess) e = grab(&ac->grad, sizeof(float) * ncell);
@@ -91,7 +92,6 @@ int adjoint_prepare(ws_t ws, const char *who, int *kern_out, ws::StreamTiling *t
         ac->kern = kern;
         ac->tx = ws->tiling.tx;
         ac->ty = ws->tiling.ty;
-    } else {
     }
     *kern_out = kern;
     *tiling_out = tiling;
@@ -101,40 +101,203 @@ int adjoint_prepare(ws_t ws, const char *who, int *kern_out, ws::StreamTiling *t
 
 // The forward run from rest over N steps: traces recorded, checkpoint pairs
 // (u^{jC}, u^{jC-1}) saved; the cache then holds this model version's run.
-int adjoint_forward(ws_t ws, AdjointCache *ac, int kern, const ws::StreamTiling &tiling) {
-    const ws::Geom &g = ws->g;
-    const int N = ws->nt_max;
-    const int C = (int)std::ceil(std::sqrt((double)N));
-    const size_t fb = field_bytes(g);
-    const size_t ntr = size_t(ws->nrec) * N;
+// forward_begin resets the state, forward_step issues step n.
+int forward_begin(ws_t ws, AdjointCache *ac) {
+    const size_t fb = field_bytes(ws->g);
+    const size_t ntr = size_t(ws->nrec) * ws->nt_max;
     const cudaStream_t st = ws->stream;
-    std::vector<float *> &ck = ac->ck;
-    int rc = WS_OK;
     ac->fwd_valid = false;
     for (int b = 0; b < 2; ++b) WS_CUDA(cudaMemsetAsync(ws->buf[b], 0, fb, st), "zero fields");
     WS_CUDA(cudaMemsetAsync(ws->traces, 0, sizeof(float) * ntr, st), "zero traces");
     ws->step = 0;
     ws->trace_start = 0;
-    ws::StepArgs a = base_args(ws);
-    for (int n = 0; n < N; ++n) {
-        if (n > 0 && n % C == 0) {
-            const int j = n / C;
-            WS_CUDA(cudaMemcpyAsync(ck[2 * (j - 1)], ws->buf[ws->cur], fb, cudaMemcpyDeviceToDevice, st),
-                    "save checkpoint");
-            WS_CUDA(cudaMemcpyAsync(ck[2 * (j - 1) + 1], ws->buf[1 - ws->cur], fb,
-                                    cudaMemcpyDeviceToDevice, st),
-                    "save checkpoint");
-        }
-        const int c = ws->cur;
-        rc = step_fp32(ws, a, kern, tiling, ws->buf[c], &ws->tmap_halo[c], ws->buf[1 - c],
+    return WS_OK;
+}
+
+int forward_step(ws_t ws, AdjointCache *ac, int kern, const ws::StreamTiling &tiling,
+                 ws::StepArgs &a, int n) {
+    const int C = (int)std::ceil(std::sqrt((double)ws->nt_max));
+    const size_t fb = field_bytes(ws->g);
+    const cudaStream_t st = ws->stream;
+    std::vector<float *> &ck = ac->ck;
+    if (n > 0 && n % C == 0) {
+        const int j = n / C;
+        WS_CUDA(cudaMemcpyAsync(ck[2 * (j - 1)], ws->buf[ws->cur], fb, cudaMemcpyDeviceToDevice, st),
+                "save checkpoint");
+        WS_CUDA(cudaMemcpyAsync(ck[2 * (j - 1) + 1], ws->buf[1 - ws->cur], fb,
+                                cudaMemcpyDeviceToDevice, st),
+                "save checkpoint");
+    }
+    const int c = ws->cur;
+    int rc = step_fp32(ws, a, kern, tiling, ws->buf[c], &ws->tmap_halo[c], ws->buf[1 - c],
                        &ws->tmap_tile[1 - c], ws->buf[1 - c], n, true, true);
-        if (rc != WS_OK) return rc;
-        ws->cur = 1 - c;
-        ws->step++;
+    if (rc != WS_OK) return rc;
+    ws->cur = 1 - c;
+    ws->step++;
+    if (n == ws->nt_max - 1) {
+        ac->fwd_valid = true;
+        ac->fwd_version = ws->model_version;
+    }
+    return WS_OK;
+}
+
+int adjoint_forward(ws_t ws, AdjointCache *ac, int kern, const ws::StreamTiling &tiling) {
+    int rc = forward_begin(ws, ac);
+    ws::StepArgs a = base_args(ws);
+    for (int n = 0; n < ws->nt_max && rc == WS_OK; ++n) rc = forward_step(ws, ac, kern, tiling, a, n);
+    return rc;
+}
+
+// One shot of a gradient run: its handle, scratch and kernel choice, its data
+// on the device, and where its gradient goes.
+struct GradShot {
+    ws_t ws = nullptr;
+    AdjointCache *ac = nullptr;
+    int kern = WS_KERNEL_STREAM;
+    ws::StreamTiling tiling{};
+    const float *d = nullptr;
+    float *grad = nullptr;
+    bool forward = true;     // run the forward problem (not reused from ws_forward)
+    ws::StepArgs a{};
+    int rho_cur = 0;         // rho[rho_cur] = rho^{k+1}
+};
+
+// The gradients of n shots with one grid and one step count, each shot's
+// work on its handle's stream, the shots interleaved step by step.
+int gradient_run(GradShot *sh, int n, int mode) {
+    const ws::Geom &g = sh[0].ws->g;
+    const int N = sh[0].ws->nt_max;
+    const int C = (int)std::ceil(std::sqrt((double)N));    // states per segment
+    const int nck = (N + C - 1) / C;                        // segments
+    const size_t fb = field_bytes(g);
+    const int np = ws::residual_partial_count();
+    for (int q = 0; q < n; ++q) {
+        GradShot &x = sh[q];
+        const cudaStream_t st = x.ws->stream;
+        for (auto &f : x.ac->rho) WS_CUDA(cudaMemsetAsync(f.p, 0, fb, st), "zero adjoint field");
+        WS_CUDA(cudaMemsetAsync(x.ac->acc, 0, 2 * fb, st), "zero gradient accumulator");
+        WS_CUDA(cudaMemcpyAsync(x.ac->rec, x.ws->rec_ijk.data(), sizeof(int) * 3 * x.ws->nrec,
+                                cudaMemcpyHostToDevice, st),
+                "upload receivers");
+        // a residual given for the run that ws_forward left in the cache (same
+        // model version) needs no new forward run
+        x.forward = !(mode == WS_ADJ_RESIDUAL && x.ac->fwd_valid &&
+                      x.ac->fwd_version == x.ws->model_version);
+        if (x.forward) {
+            int rc = forward_begin(x.ws, x.ac);
+            if (rc != WS_OK) return rc;
+        }
+        x.a = base_args(x.ws);
+        x.rho_cur = 0;
     }
 
-    ac->fwd_valid = true;
-    ac->fwd_version = ws->model_version;
+    // 1. forward from rest, recording the traces and the checkpoints
+    for (int t = 0; t < N; ++t)
+        for (int q = 0; q < n; ++q)
+            if (sh[q].forward) {
+                int rc = forward_step(sh[q].ws, sh[q].ac, sh[q].kern, sh[q].tiling, sh[q].a, t);
+                if (rc != WS_OK) return rc;
+            }
+
+    // 2. residual and misfit
+    for (int q = 0; q < n; ++q) {
+        GradShot &x = sh[q];
+        const long long ntr = (long long)x.ws->nrec * N;
+        WS_CUDA(ws::launch_residual(mode == WS_ADJ_DATA ? x.ws->traces : x.d,
+                                    mode == WS_ADJ_DATA ? x.d : nullptr, ntr, x.ac->r,
+                                    x.ac->partials, x.ac->partials + np, x.ws->stream),
+                "residual kernels");
+        x.ws->launches += 2;
+    }
+
+    // 3. backward: rho^k, k = N .. 1, segment by segment, the segment's
+    // states recomputed from its checkpoint
+    for (int j = nck - 1; j >= 0; --j) {
+        const int n0 = j * C, n1 = std::min(n0 + C, N);
+        // u^{n0}, u^{n0-1} into the ring, then steps n0 .. n1-1, each storing
+        // L u^n into lap[n - n0] (u^{n1} itself is not needed)
+        for (int q = 0; q < n; ++q) {
+            AdjointCache *ac = sh[q].ac;
+            const cudaStream_t st = sh[q].ws->stream;
+            if (j == 0) {
+                WS_CUDA(cudaMemsetAsync(ac->ring[0].p, 0, fb, st), "zero initial state");
+                WS_CUDA(cudaMemsetAsync(ac->ring[1].p, 0, fb, st), "zero initial state");
+            } else {
+                WS_CUDA(cudaMemcpyAsync(ac->ring[0].p, ac->ck[2 * (j - 1)], fb,
+                                        cudaMemcpyDeviceToDevice, st),
+                        "restore checkpoint");
+                WS_CUDA(cudaMemcpyAsync(ac->ring[1].p, ac->ck[2 * (j - 1) + 1], fb,
+                                        cudaMemcpyDeviceToDevice, st),
+                        "restore checkpoint");
+            }
+        }
+        for (int t = 0; t < n1 - n0; ++t)
+            for (int q = 0; q < n; ++q) {
+                GradShot &x = sh[q];
+                const int uc = t & 1;   // ring[uc] = u^{n0+t}
+                MappedField &un = x.ac->ring[uc], &um = x.ac->ring[1 - uc];
+                x.a.lap = x.ac->lap[t];
+                int rc = step_fp32(x.ws, x.a, x.kern, x.tiling, un.p, &un.halo, um.p, &um.tile,
+                                   um.p, n0 + t, true, false);
+                x.a.lap = nullptr;
+                if (rc != WS_OK) return rc;
+            }
+        for (int k = n1; k > n0; --k)
+            for (int q = 0; q < n; ++q) {
+                GradShot &x = sh[q];
+                ws_t ws = x.ws;
+                MappedField *rho = x.ac->rho;
+                MappedField &r1 = rho[x.rho_cur], &r2 = rho[1 - x.rho_cur];
+                int rc = step_fp32(ws, x.a, x.kern, x.tiling, r1.p, &r1.halo, r2.p, &r2.tile, r2.p,
+                                   k, false, false);
+                if (rc != WS_OK) return rc;
+                x.rho_cur = 1 - x.rho_cur;   // rho[rho_cur] = rho^k
+                WS_CUDA(ws::launch_inject(rho[x.rho_cur].p, ws->w, ws->gx, ws->gy, ws->gz, g,
+                                          x.ac->rec, ws->nrec, x.ac->r, N, k - 1, ws->stream),
+                        "adjoint injection kernel");
+                ws::Sources src{};
+                sources_of_step(ws, k - 1, &src);
+                WS_CUDA(ws::launch_imaging(rho[x.rho_cur].p, x.ac->lap[k - 1 - n0], g, src, ws->gx,
+                                           ws->gy, ws->gz, x.ac->acc, ws->stream),
+                        "gradient imaging kernel");
+                ws->launches += 2;
+            }
+    }
+    for (int q = 0; q < n; ++q) {
+        ws_t ws = sh[q].ws;
+        const double hdt = ws->h / ws->dt;
+        WS_CUDA(ws::launch_finalize_gradient(sh[q].ac->acc, ws->w, g, hdt * hdt, sh[q].grad,
+                                             ws->stream),
+                "gradient finalize kernel");
+        ws->launches++;
+    }
+    return WS_OK;
+}
+
+// After a run: every shot's stream drained; *misfit = the summed misfits
+// (host, fixed order); TIMEOUT if a bounded device wait ran out in any shot.
+int gradient_finish(GradShot *sh, int n, double *misfit) {
+    const int np = ws::residual_partial_count();
+    double J = 0.0;
+    bool timeout = false;
+    for (int q = 0; q < n; ++q) {
+        ws_t ws = sh[q].ws;
+        double j = 0.0;
+        WS_CUDA(cudaMemcpyAsync(&j, sh[q].ac->partials + np, sizeof(double), cudaMemcpyDeviceToHost,
+                                ws->stream),
+                "copy misfit");
+        WS_CUDA(cudaStreamSynchronize(ws->stream), "ws_adjoint_gradient");
+        J += j;
+        unsigned status = 0;
+        WS_CUDA(cudaMemcpy(&status, ws->status, sizeof status, cudaMemcpyDeviceToHost),
+                "ws_adjoint_gradient");
+        if (status & ws::kStatusTimeout) {
+            WS_CUDA(cudaMemset(ws->status, 0, sizeof(unsigned)), "ws_adjoint_gradient");
+            timeout = true;
+        }
+    }
+    if (misfit) *misfit = J;
+    if (timeout) return fail(WS_ERR_TIMEOUT, "a bounded device wait ran out in a step kernel");
     return WS_OK;
 }
 
@@ -157,118 +320,101 @@ int ws_adjoint_gradient(ws_t ws, const float *data, int mode, float *grad_m, dou
     if (!ws || !data || !grad_m) return fail(WS_ERR_BADARG, "ws_adjoint_gradient: NULL argument");
     if (mode != WS_ADJ_DATA && mode != WS_ADJ_RESIDUAL)
         return fail(WS_ERR_BADARG, "ws_adjoint_gradient: unknown mode %d", mode);
-    int kern = WS_KERNEL_STREAM;
-    ws::StreamTiling tiling{};
-    AdjointCache *ac = nullptr;
-    int rc = adjoint_prepare(ws, "ws_adjoint_gradient", &kern, &tiling, &ac);
+    GradShot x;
+    x.ws = ws;
+    int rc = adjoint_prepare(ws, "ws_adjoint_gradient", &x.kern, &x.tiling, &x.ac);
     if (rc != WS_OK) return rc;
-    const ws::Geom &g = ws->g;
-    const int N = ws->nt_max;
-    const int C = (int)std::ceil(std::sqrt((double)N));    // states per segment
-    const int nck = (N + C - 1) / C;                        // segments
-    const size_t fb = field_bytes(g);
-    const size_t ncell = size_t(g.nx) * g.ny * g.nz;
-    const size_t ntr = size_t(ws->nrec) * N;
-    const cudaStream_t st = ws->stream;
-    for (auto &f : ac->rho) WS_CUDA(cudaMemsetAsync(f.p, 0, fb, st), "zero adjoint field");
-    std::vector<float *> &ck = ac->ck;
-    std::vector<float *> &lap = ac->lap;
-    MappedField *ring = ac->ring;
-    MappedField *rho = ac->rho;
-    float2 *acc = ac->acc;
-    double *partials = ac->partials;
-    float *r = ac->r, *grad = on_device ? grad_m : ac->grad;
-    const float *d = data;
-    int *rec = ac->rec;
-    const int np = ws::residual_partial_count();
-    WS_CUDA(cudaMemsetAsync(acc, 0, 2 * fb, st), "zero gradient accumulator");
-    WS_CUDA(cudaMemcpyAsync(rec, ws->rec_ijk.data(), sizeof(int) * 3 * ws->nrec,
-                            cudaMemcpyHostToDevice, st),
-            "upload receivers");
+    const size_t ncell = size_t(ws->g.nx) * ws->g.ny * ws->g.nz;
+    const size_t ntr = size_t(ws->nrec) * ws->nt_max;
+    x.d = data;
     if (!on_device) {
-        WS_CUDA(cudaMemcpyAsync(ac->dd, data, sizeof(float) * ntr, cudaMemcpyHostToDevice, st),
+        WS_CUDA(cudaMemcpyAsync(x.ac->dd, data, sizeof(float) * ntr, cudaMemcpyHostToDevice,
+                                ws->stream),
                 "upload observed data");
-        d = ac->dd;
+        x.d = x.ac->dd;
     }
-
-    // 1. forward from rest, recording the traces and the checkpoints; a
-    // residual given for the run that ws_forward left in the cache (same
-    // model version) needs no new forward run
-    if (!(mode == WS_ADJ_RESIDUAL && ac->fwd_valid && ac->fwd_version == ws->model_version)) {
-        rc = adjoint_forward(ws, ac, kern, tiling);
-        if (rc != WS_OK) return rc;
-    }
-    ws::StepArgs a = base_args(ws);
-
-    // 2. residual and misfit
-    WS_CUDA(ws::launch_residual(mode == WS_ADJ_DATA ? ws->traces : d,
-                                mode == WS_ADJ_DATA ? d : nullptr, (long long)ntr, r, partials,
-                                partials + np, st),
-            "residual kernels");
-    ws->launches += 2;
-
-    // 3. backward: rho^k, k = N .. 1, segment by segment, the segment's
-    // states recomputed from its checkpoint
-    int rc_cur = 0;   // rho[rc_cur] = rho^{k+1}, rho[1 - rc_cur] = rho^{k+2}
-    for (int j = nck - 1; j >= 0; --j) {
-        const int n0 = j * C, n1 = std::min(n0 + C, N);
-        // u^{n0}, u^{n0-1} into the ring, then steps n0 .. n1-1, each storing
-        // L u^n into lap[n - n0] (u^{n1} itself is not needed)
-        if (j == 0) {
-            WS_CUDA(cudaMemsetAsync(ring[0].p, 0, fb, st), "zero initial state");
-            WS_CUDA(cudaMemsetAsync(ring[1].p, 0, fb, st), "zero initial state");
-        } else {
-            WS_CUDA(cudaMemcpyAsync(ring[0].p, ck[2 * (j - 1)], fb, cudaMemcpyDeviceToDevice, st),
-                    "restore checkpoint");
-            WS_CUDA(cudaMemcpyAsync(ring[1].p, ck[2 * (j - 1) + 1], fb, cudaMemcpyDeviceToDevice, st),
-                    "restore checkpoint");
-        }
-        int uc = 0;   // ring[uc] = u^n
-        for (int t = 0; t < n1 - n0; ++t) {
-            MappedField &un = ring[uc], &um = ring[1 - uc];
-            a.lap = lap[t];
-            rc = step_fp32(ws, a, kern, tiling, un.p, &un.halo, um.p, &um.tile, um.p, n0 + t, true,
-                           false);
-            a.lap = nullptr;
-            if (rc != WS_OK) return rc;
-            uc = 1 - uc;
-        }
-        for (int k = n1; k > n0; --k) {
-            MappedField &r1 = rho[rc_cur], &r2 = rho[1 - rc_cur];
-            rc = step_fp32(ws, a, kern, tiling, r1.p, &r1.halo, r2.p, &r2.tile, r2.p, k, false,
-                           false);
-            if (rc != WS_OK) return rc;
-            rc_cur = 1 - rc_cur;   // rho[rc_cur] = rho^k
-            WS_CUDA(ws::launch_inject(rho[rc_cur].p, ws->w, ws->gx, ws->gy, ws->gz, g, rec,
-                                      ws->nrec, r, N, k - 1, st),
-                    "adjoint injection kernel");
-            ws::Sources src{};
-            sources_of_step(ws, k - 1, &src);
-            WS_CUDA(ws::launch_imaging(rho[rc_cur].p, lap[k - 1 - n0], g, src, ws->gx, ws->gy,
-                                       ws->gz, acc, st),
-                    "gradient imaging kernel");
-            ws->launches += 2;
-        }
-    }
-    const double hdt = ws->h / ws->dt;
-    WS_CUDA(ws::launch_finalize_gradient(acc, ws->w, g, hdt * hdt, grad, st),
-            "gradient finalize kernel");
-    ws->launches++;
+    x.grad = on_device ? grad_m : x.ac->grad;
+    rc = gradient_run(&x, 1, mode);
+    if (rc != WS_OK) return rc;
     if (!on_device)
-        WS_CUDA(cudaMemcpyAsync(grad_m, grad, sizeof(float) * ncell, cudaMemcpyDeviceToHost, st),
+        WS_CUDA(cudaMemcpyAsync(grad_m, x.grad, sizeof(float) * ncell, cudaMemcpyDeviceToHost,
+                                ws->stream),
                 "copy gradient");
-    double J = 0.0;
-    WS_CUDA(cudaMemcpyAsync(&J, partials + np, sizeof(double), cudaMemcpyDeviceToHost, st),
-            "copy misfit");
-    WS_CUDA(cudaStreamSynchronize(st), "ws_adjoint_gradient");
-    if (misfit) *misfit = J;
-    unsigned status = 0;
-    WS_CUDA(cudaMemcpy(&status, ws->status, sizeof status, cudaMemcpyDeviceToHost),
-            "ws_adjoint_gradient");
-    if (status & ws::kStatusTimeout) {
-        WS_CUDA(cudaMemset(ws->status, 0, sizeof(unsigned)), "ws_adjoint_gradient");
-        return fail(WS_ERR_TIMEOUT, "a bounded device wait ran out in a step kernel");
+    return gradient_finish(&x, 1, misfit);
+}
+
+int ws_adjoint_gradient_shots(ws_t *shots, int nshots, const float *const *data, int mode,
+                              float *grad_m, double *misfit, double *grad_norm, int on_device) {
+    if (!shots || !data || !grad_m)
+        return fail(WS_ERR_BADARG, "ws_adjoint_gradient_shots: NULL argument");
+    if (nshots < 1 || nshots > WS_MAX_SHOTS)
+        return fail(WS_ERR_BADARG, "ws_adjoint_gradient_shots: nshots must be in [1, %d], got %d",
+                    WS_MAX_SHOTS, nshots);
+    if (mode != WS_ADJ_DATA && mode != WS_ADJ_RESIDUAL)
+        return fail(WS_ERR_BADARG, "ws_adjoint_gradient_shots: unknown mode %d", mode);
+    for (int q = 0; q < nshots; ++q) {
+        if (!shots[q] || !data[q])
+            return fail(WS_ERR_BADARG, "ws_adjoint_gradient_shots: NULL handle or data of shot %d", q);
+        const ws::Geom &g = shots[q]->g, &g0 = shots[0]->g;
+        if (g.nx != g0.nx || g.ny != g0.ny || g.nz != g0.nz || shots[q]->nt_max != shots[0]->nt_max)
+            return fail(WS_ERR_BADARG,
+                        "ws_adjoint_gradient_shots: shot %d differs from shot 0 in grid size or "
+                        "step count",
+                        q);
+        for (int p = 0; p < q; ++p)
+            if (shots[p] == shots[q])
+                return fail(WS_ERR_BADARG, "ws_adjoint_gradient_shots: handle given twice (%d, %d)",
+                            p, q);
     }
+    std::vector<GradShot> sh(nshots);
+    for (int q = 0; q < nshots; ++q) {
+        GradShot &x = sh[q];
+        x.ws = shots[q];
+        int rc = adjoint_prepare(x.ws, "ws_adjoint_gradient_shots", &x.kern, &x.tiling, &x.ac);
+        if (rc != WS_OK) return rc;
+        x.d = data[q];
+        if (!on_device) {
+            WS_CUDA(cudaMemcpyAsync(x.ac->dd, data[q],
+                                    sizeof(float) * size_t(x.ws->nrec) * x.ws->nt_max,
+                                    cudaMemcpyHostToDevice, x.ws->stream),
+                    "upload observed data");
+            x.d = x.ac->dd;
+        }
+        x.grad = x.ac->grad;   // each shot's own gradient, summed below
+    }
+    int rc = gradient_run(sh.data(), nshots, mode);
+    if (rc != WS_OK) return rc;
+    // the sum on shot 0's stream, after every shot's gradient
+    ws_t w0 = shots[0];
+    const cudaStream_t s0 = w0->stream;
+    const long long ncell = (long long)w0->g.nx * w0->g.ny * w0->g.nz;
+    for (int q = 1; q < nshots; ++q) {
+        cudaEvent_t ev;
+        WS_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "ws_adjoint_gradient_shots");
+        cudaError_t e = cudaEventRecord(ev, shots[q]->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s0, ev, 0);
+        cudaEventDestroy(ev);
+        WS_CUDA(e, "ws_adjoint_gradient_shots");
+    }
+    ws::FieldList list{};
+    for (int q = 0; q < nshots; ++q) list.p[q] = sh[q].grad;
+    float *out = on_device ? grad_m : sh[0].ac->grad;
+    WS_CUDA(ws::launch_sum_fields(list, nshots, ncell, out, s0), "gradient sum kernel");
+    w0->launches++;
+    double *norm = sh[0].ac->norm;
+    const int np = ws::residual_partial_count();
+    WS_CUDA(ws::launch_norm2(out, ncell, norm, norm + np, s0), "gradient norm kernels");
+    w0->launches += 3;
+    if (!on_device)
+        WS_CUDA(cudaMemcpyAsync(grad_m, out, sizeof(float) * size_t(ncell), cudaMemcpyDeviceToHost,
+                                s0),
+                "copy gradient");
+    double gn = 0.0;
+    WS_CUDA(cudaMemcpyAsync(&gn, norm + np, sizeof(double), cudaMemcpyDeviceToHost, s0),
+            "copy gradient norm");
+    rc = gradient_finish(sh.data(), nshots, misfit);
+    if (rc != WS_OK) return rc;
+    if (grad_norm) *grad_norm = gn;
     return WS_OK;
 }
 

@@ -96,6 +96,8 @@ struct ws_handle {
     CUtensorMap t16_halo[2], t16_d, t16_w;
     double wmax = 0.0;         // max (V dt / h)^2 of the model
     ws::Free16 free16{};       // cells whose taper is exactly 1, per axis
+    int tile16_y = 0;          // 16-bit tile height chosen by ws_set_kernel (0: default)
+    int t16_ty = 0;            // tile height the 16-bit tensor maps are encoded for
 
     // device scratch of ws_adjoint_gradient, kept for the next call
     struct AdjointCache *adj = nullptr;
@@ -124,7 +126,8 @@ struct AdjointCache {
     std::vector<float *> lap;       // L u^n of the segment's steps
     MappedField ring[2], rho[2];    // recomputed u^n / u^{n-1}; rho^{k+1} / rho^{k+2}
     float2 *acc = nullptr;          // compensated FP32 gradient sums, padded layout
-    double *partials = nullptr;
+    double *partials = nullptr;     // residual partial sums, then the misfit
+    double *norm = nullptr;         // gradient-norm partial sums, then the norm
     float *r = nullptr, *dd = nullptr, *grad = nullptr;
     int *rec = nullptr;
     ~AdjointCache() {
@@ -155,10 +158,17 @@ int build_rec_tiles(ws_t ws, const ws::StreamTiling &t, int rows = 1);
 int copy_in(ws_t ws, float *dst, const float *src, int on_device);
 int copy_out(ws_t ws, float *dst, const float *src, int on_device);
 int upload_profiles(ws_t ws);
-// The tile of the 16-bit streaming kernel and the rows each of its consumer
-// threads computes.
-constexpr int kTile16X = 64, kTile16Y = 16, kRows16 = 2;
-int encode_maps16(ws_t ws);
+// The tile of the 16-bit streaming kernel (64 x ty) and the rows each of its
+// threads computes. The default tile height is the first of kTile16Ys that
+// the grid holds: 24 (two CTAs of 6 warps per SM) measured fastest on the
+// 1024^3 survey (FP16 434.7, BF16 436.5 Gcell/s, against 418 for 48 and 395
+// for 16); 48 is selectable with ws_set_kernel.
+constexpr int kTile16X = 64, kRows16 = 2;
+constexpr int kTile16Ys[] = {24, 16};
+constexpr int kNumTile16Ys = 2;
+int pick_tile16(const ws_t ws);
+int default_zblock16(const ws::Geom &g, int ty);
+int encode_maps16(ws_t ws, int ty);
 int encode_state16(ws_t ws);
 int decode_state16(ws_t ws);
 // Point sources of step n (amp = h^2 s(t_n)).

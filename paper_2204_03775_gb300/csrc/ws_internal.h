@@ -175,16 +175,21 @@ struct Free16 {
 };
 Weights16 zero_sum_weights16();
 bool stream16_tiling_supported(int tx, int ty);
-// tmap_u: U (16-bit) with box (tx+16, ty+8, 1); tmap_d: D and tmap_w: the
-// 16-bit model, both with box (tx, ty, 1). u_out receives U' (the other U
-// buffer); D is updated in place at d_io. src_hint: bound on
+// SMs x resident CTAs of the 16-bit kernel with 64 x ty tiles.
+cudaError_t stream16_slots(int ty, int *slots);
+// The tensor maps of a 16-bit step: u: U (16-bit) with box (tx+16, ty+8, 1);
+// d: D and w: the 16-bit model, both with box (tx, ty, 1); u_out receives U'
+// (the other U buffer), D is updated in place at d_io. src_hint: bound on
 // |(V dt)^2 s(t_n)| of this step's sources (picks the output exponents while
 // the field is still zero).
-cudaError_t launch_step_stream16(int storage, const CUtensorMap *tmap_u, const CUtensorMap *tmap_d,
-                                 const CUtensorMap *tmap_w, uint16_t *u_out, uint16_t *d_io,
-                                 const StepArgs &a, Scale16 *sc, long long step, float src_hint,
-                                 const Free16 &fr, const StreamTiling &t, const int *rec_ptr,
-                                 const RecEntry *rec, cudaStream_t s);
+struct Maps16In {
+    const CUtensorMap *u, *d, *w;
+    uint16_t *u_out, *d_io;
+};
+cudaError_t launch_step_stream16(int storage, const Maps16In &m, const StepArgs &a, Scale16 *sc,
+                                 long long step, float src_hint, const Free16 &fr,
+                                 const StreamTiling &t, const int *rec_ptr, const RecEntry *rec,
+                                 cudaStream_t s);
 // FP32 padded (u^n, u^{n-1}) <-> 16-bit padded (U, D) (interior), exponent slot `slot`.
 cudaError_t launch_encode16(int storage, const float *u, const float *up, uint16_t *U, uint16_t *D,
                             const Geom &g, Scale16 *sc, int slot, cudaStream_t s);
@@ -210,6 +215,18 @@ cudaError_t launch_inject(float *rho, const float *w, const float *gx, const flo
 cudaError_t launch_imaging(const float *rho, const float *lapu, const Geom &g, const Sources &src,
                            const float *gx, const float *gy, const float *gz, float2 *acc,
                            cudaStream_t s);
+// out[t] = sum over q < n of src.p[q][t], t < count (FP64 sum in the order of
+// q, rounded once); out may be src.p[0]. n <= kMaxFieldList.
+constexpr int kMaxFieldList = WS_MAX_SHOTS;
+struct FieldList {
+    const float *p[kMaxFieldList];
+};
+cudaError_t launch_sum_fields(const FieldList &src, int n, long long count, float *out,
+                              cudaStream_t s);
+// *out = sqrt(sum x^2) in FP64 over n floats: per-block partial sums into
+// partials[residual_partial_count()], then their fixed-order sum.
+cudaError_t launch_norm2(const float *x, long long n, double *partials, double *out,
+                         cudaStream_t s);
 // grad (unpadded float) = -V^2 (sum - correction) of acc, V^2 = W (h / dt)^2.
 cudaError_t launch_finalize_gradient(const float2 *acc, const float *w, const Geom &g,
                                      double h_over_dt2, float *grad, cudaStream_t s);

@@ -150,9 +150,64 @@ __global__ void finalize_kernel(const float2 *__restrict__ acc, const float *__r
     grad[o] = -w[p] * (float)h_over_dt2 * (a.x - a.y);
 }
 
+// out = sum over shots s = 0 .. n-1 of src[s] (FP64 sum in shot order, rounded
+// once); out may be src[0].
+__global__ void sum_fields_kernel(FieldList src, int n, long long count, float *out) {
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < count;
+         t += (long long)gridDim.x * blockDim.x) {
+        double acc = 0.0;
+        for (int q = 0; q < n; ++q) acc += (double)src.p[q][t];
+        out[t] = (float)acc;
+    }
+}
+
+// Per-block FP64 partial sums of x^2 (a fixed grid: the same blocks sum the
+// same elements on every call).
+__global__ void __launch_bounds__(kRedThreads) norm2_partials_kernel(const float *__restrict__ x,
+                                                                     long long n,
+                                                                     double *__restrict__ partials) {
+    double acc = 0.0;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+         t += (long long)gridDim.x * blockDim.x)
+        acc = fma((double)x[t], (double)x[t], acc);
+    __shared__ double ws[kRedThreads / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        acc = threadIdx.x < kRedThreads / 32 ? ws[threadIdx.x] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+        if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+    }
+}
+
+__global__ void sqrt_kernel(double *x) { x[0] = sqrt(x[0]); }
+
 }  // namespace
 
 int residual_partial_count() { return 1024; }
+
+cudaError_t launch_sum_fields(const FieldList &src, int n, long long count, float *out,
+                              cudaStream_t s) {
+    if (n < 1 || n > kMaxFieldList) return cudaErrorInvalidValue;
+    sum_fields_kernel<<<1216, 256, 0, s>>>(src, n, count, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_norm2(const float *x, long long n, double *partials, double *out,
+                         cudaStream_t s) {
+    const int blocks = residual_partial_count();
+    norm2_partials_kernel<<<blocks, kRedThreads, 0, s>>>(x, n, partials);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    sum_kernel<<<1, kRedThreads, 0, s>>>(partials, blocks, out);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    sqrt_kernel<<<1, 1, 0, s>>>(out);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_residual(const float *traces, const float *d_obs, long long n, float *r,
                             double *partials, double *misfit, cudaStream_t s) {

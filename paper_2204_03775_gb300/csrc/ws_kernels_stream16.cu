@@ -162,17 +162,23 @@ struct Cfg16 {
     static constexpr int kSW = TX + 2 * kHalo;
     static constexpr int kStage = kSW * kRows;
     // halo cells decoded per plane, in units of 4 cells: 2*TX units in the 8
-    // rows above and below the tile (one per thread), 2*TY = 32 units beside
-    // it (the last warp, one per lane)
-    static constexpr int kSideWarp = kWarps - 1;
-    static_assert(kThreads % 32 == 0, "whole warps");
-    static_assert(TX % 64 == 0 && TY == 16, "64-wide tiles of 16 rows (8 row pairs)");
-    static_assert(2 * TX == kThreads && 2 * TY == 32, "one band unit per thread, one side warp");
+    // rows above and below the tile, 2*TY units beside it; thread t decodes
+    // unit t and, when there are more units than threads, unit t + kThreads
+    static constexpr int kBandUnits = 2 * TX;
+    static constexpr int kUnits = kBandUnits + 2 * TY;
+    static constexpr bool kAllFirst = kUnits >= kThreads;   // every thread has a first unit
+    static constexpr bool kSecond = kUnits > kThreads;      // some threads have a second one
+    // CTAs per SM that the register file holds at up to 168 registers a thread
+    static constexpr int kMinBlocks = 384 / kThreads;
+    static_assert(kThreads % 32 == 0 && kMinBlocks >= 1, "whole warps, 128 .. 384 threads");
+    static_assert(TX == 64 && TY % 4 == 0 && kBandUnits <= kThreads && kUnits <= 2 * kThreads,
+                  "64-wide tiles; one or two halo units per thread");
+    static constexpr unsigned kStageBytes = kStage * 4u;
     static_assert(NA == 9 && NB == 3, "ring slots are compile-time constants of a 9-plane trip");
-    static_assert(kSlotABytes % 128 == 0 && kSlotBBytes % 128 == 0 && (kStage * 4) % 128 == 0,
+    static_assert(kSlotABytes % 128 == 0 && kSlotBBytes % 128 == 0 && kStageBytes % 128 == 0,
                   "slots stay 128-byte aligned");
     static constexpr size_t kSmem =
-        size_t(2 * kStage) * 4u + size_t(NA) * kSlotABytes + size_t(NB) * kSlotBBytes;
+        size_t(2) * kStageBytes + size_t(NA) * kSlotABytes + size_t(NB) * kSlotBBytes;
 };
 
 // 128-bit shared store.
@@ -185,6 +191,35 @@ __device__ __forceinline__ void sts4(float *p, float4 v) {
 struct Maps16 {
     CUtensorMap u, d, w;
 };
+
+// Shared-memory accesses at a 32-bit shared address plus a compile-time byte
+// offset: every ring and staging access of a plane is one instruction with an
+// immediate offset from a per-thread base computed once per item.
+template <int OFF>
+__device__ __forceinline__ uint2 lds2_at(unsigned a) {
+    uint2 v;
+    asm volatile("ld.shared.v2.u32 {%0, %1}, [%2+%3];" : "=r"(v.x), "=r"(v.y) : "r"(a), "n"(OFF));
+    return v;
+}
+template <int OFF>
+__device__ __forceinline__ float4 lds4_at(unsigned a) {
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4+%5];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "r"(a), "n"(OFF));
+    return v;
+}
+template <int OFF>
+__device__ __forceinline__ void sts4_at(unsigned a, float4 v) {
+    asm volatile("st.shared.v4.f32 [%0+%1], {%2, %3, %4, %5};" ::"r"(a), "n"(OFF), "f"(v.x),
+                 "f"(v.y), "f"(v.z), "f"(v.w)
+                 : "memory");
+}
+
+// The stencil weights (zero_sum_weights16() times 2^-kW16Exp) as compile-time
+// constants; the launcher checks them against the host computation.
+constexpr float kW16C0 = -0x1.11555cp-9f, kW16C1 = 0x1.9999a4p-12f, kW16C2 = -0x1.9999ap-15f,
+                kW16C3 = 0x1.a01ap-18f, kW16C4 = -0x1.d42p-22f;
 
 // Barriers of one CTA: a "full" mbarrier per ring slot (transaction bytes);
 // no "empty" barriers: a slot is refilled right after the plane barrier
@@ -277,21 +312,6 @@ __device__ __forceinline__ void inject_sources(float4 *dn, const float4 *wr, uns
     }
 }
 
-// Stores of a thread with cells outside the grid (nvalid < 4 or no row j+1).
-__device__ __forceinline__ void store_partial(uint16_t *p, long long d_delta, int pitch, uint2 su0,
-                                              uint2 sd0, uint2 su1, uint2 sd1, int nvalid,
-                                              bool row1) {
-    const uint2 su[2] = {su0, su1}, sd[2] = {sd0, sd1};
-    for (int r = 0; r < (row1 ? 2 : 1); ++r) {
-        uint16_t *o = p + r * pitch;
-        for (int l = 0; l < nvalid; ++l) {
-            const unsigned wu = l < 2 ? su[r].x : su[r].y, wd = l < 2 ? sd[r].x : sd[r].y;
-            o[l] = (uint16_t)((l & 1) ? (wu >> 16) : (wu & 0xffffu));
-            o[l + d_delta] = (uint16_t)((l & 1) ? (wd >> 16) : (wd & 0xffffu));
-        }
-    }
-}
-
 // Receivers of plane k, values u~ in stored units times 2^r2t (true units);
 // returns the new (cursor, next plane).
 __device__ __forceinline__ int2 record16(float4 u0, float4 u1, int r2t, int k, int rcur, int rend,
@@ -314,21 +334,58 @@ struct Walk16 {
     bool ok;
 };
 
-// What a thread needs of its item, fixed over the walk.
+// What a thread needs of its item, fixed over the walk. Shared addresses are
+// 32-bit byte addresses of the thread's own place in ring slot 0 / staging
+// buffer 0; the slot and buffer offsets are compile-time constants.
 struct Ctx16 {
-    const uint16_t *ringA, *ringB;
-    float *stage;
-    uint16_t *pu;          // U' of (i, j, z0); D at pu + d_delta, row j+1 one pitch on
-    long long d_delta, plane;
+    unsigned aOwn, aUnit1, aUnit2; // ring A: own cells (row j), halo units
+    unsigned bOwn;                 // ring B: own D cells (row j); W one tile on
+    unsigned sOwn, sUnit1, sUnit2; // staging buffer 0: own cell (row j), halo units
     const float *gz;
     float4 gxy[2];         // gx * gy of the 4 columns per row (0 outside the grid)
     int i, j, z0, z1, nb, nplanes;
-    int offA, offB, offS, band_src, band_dst, side_src, side_dst;
-    int pitch, nvalid;
-    bool row1, full, side, xy_free;
+    bool unit1, unit2, xy_free, full;
+    bool lean;             // xy_free, no source in the item, no change of scale this step
     int fz0, fz1;          // planes whose taper is exactly 1
+    int nvalid, pitch;     // valid x cells; row pitch (elements)
+    bool row1;             // row j+1 inside the grid
+    long long d_delta, plane;
     unsigned src_mask;
 };
+
+// Stores of a thread with cells outside the grid (nvalid < 4 or no row j+1).
+__device__ __forceinline__ void store_partial(uint16_t *p, long long d_delta, int pitch, uint2 su0,
+                                              uint2 sd0, uint2 su1, uint2 sd1, int nvalid,
+                                              bool row1) {
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        if (r == 1 && !row1) break;
+        const uint2 su = r ? su1 : su0, sd = r ? sd1 : sd0;
+        uint16_t *o = p + r * pitch;
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+            if (l >= nvalid) break;
+            const unsigned wu = l < 2 ? su.x : su.y, wd = l < 2 ? sd.x : sd.y;
+            o[l] = (uint16_t)((l & 1) ? (wu >> 16) : (wu & 0xffffu));
+            o[l + d_delta] = (uint16_t)((l & 1) ? (wd >> 16) : (wd & 0xffffu));
+        }
+    }
+}
+
+// u + d and x * f of 4 cells, as two FP32x2 operations each.
+__device__ __forceinline__ float4 add4(const float4 &u, const float4 &d) {
+    const float2 a = add2(lo2(u), lo2(d)), b = add2(hi2(u), hi2(d));
+    return make_float4(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ float4 mul4(const float4 &x, float f) {
+    const float2 a = mul2(lo2(x), splat(f)), b = mul2(hi2(x), splat(f));
+    return make_float4(a.x, a.y, b.x, b.y);
+}
+
+// 4 stored values (8 bytes), streaming store.
+__device__ __forceinline__ void store16(uint16_t *p, const uint2 st) {
+    asm volatile("st.global.cs.v2.u32 [%0], {%1, %2};" ::"l"(p), "r"(st.x), "r"(st.y) : "memory");
+}
 
 template <class Fmt, int TX, int TY, int NA, int NB>
 struct Kern16 {
@@ -337,7 +394,6 @@ struct Kern16 {
 
     // factors of one launch (uniform)
     struct Factors {
-        float c0, c1, c2, c3, c4;   // zero-sum weights times 2^-kW16Exp: absorb the model's factor
         float wtrue;    // stored W -> (V dt/h)^2
         float amp2r;    // source amplitude (h^2 s) -> stored U units
         float ro;       // stored U units -> the output units of U' and D'
@@ -366,12 +422,6 @@ struct Kern16 {
                     it.z0 + b + kHalo);
     }
 
-    // 4 stored values (8 bytes), streaming store.
-    static __device__ __forceinline__ void store16(uint16_t *p, const uint2 st) {
-        asm volatile("st.global.cs.v2.u32 [%0], {%1, %2};" ::"l"(p), "r"(st.x), "r"(st.y)
-                     : "memory");
-    }
-
     // The stencil sum of one row's 4 cells (two FP32x2 pairs): c0 u +
     // sum_m c_m s_m, s_m the six neighbours at distance m, each summed as
     // symmetric pairs first. xl, xr: cells x-4..x-1 and x+4..x+7 of the row;
@@ -379,8 +429,7 @@ struct Kern16 {
     template <int RQ>
     static __device__ __forceinline__ void stencil_row(const Walk16 &wk, int r, const float4 &xl,
                                                        const float4 &xr, const float4 (&yp)[4],
-                                                       const float4 (&ym)[4], const Factors &fc,
-                                                       float2 (&lap)[2]) {
+                                                       const float4 (&ym)[4], float2 (&lap)[2]) {
         const float4 xc = wk.q[(RQ + 4) % 9][r];
         const float e[12] = {xl.x, xl.y, xl.z, xl.w, xc.x, xc.y, xc.z, xc.w,
                              xr.x, xr.y, xr.z, xr.w};
@@ -407,11 +456,11 @@ struct Kern16 {
                                        pair(wk.q[(RQ + 4 - m + 9) % 9][r], p));
                 s[m] = add2(add2(sx[p][m], sy), sz);
             }
-            float2 l = mul2(splat(fc.c0), pair(xc, p));
-            l = fma2(splat(fc.c4), s[4], l);
-            l = fma2(splat(fc.c3), s[3], l);
-            l = fma2(splat(fc.c2), s[2], l);
-            lap[p] = fma2(splat(fc.c1), s[1], l);
+            float2 l = mul2(splat(kW16C0), pair(xc, p));
+            l = fma2(splat(kW16C4), s[4], l);
+            l = fma2(splat(kW16C3), s[3], l);
+            l = fma2(splat(kW16C2), s[2], l);
+            lap[p] = fma2(splat(kW16C1), s[1], l);
         }
     }
 
@@ -439,79 +488,96 @@ struct Kern16 {
         return make_float4(o[0].x, o[0].y, o[1].x, o[1].y);
     }
 
-    // Plane k of the walk, RQ = (k - z0) mod 9; tp: parity of the trip.
+    // Plane k of the walk, RQ = (k - z0) mod 9; tp: parity of the trip;
+    // so: byte offset of plane k's staging buffer; pk: U' of (i, j, k).
     template <int RQ>
     static __device__ __forceinline__ void plane_step(Walk16 &wk, const Ctx16 &cx, B &br,
-                                                      uint16_t *ringA_w, uint16_t *ringB_w,
+                                                      uint16_t *ringA, uint16_t *ringB,
                                                       const Maps16 &mp, const Item &it,
                                                       const StepArgs &a, const Factors &fc,
-                                                      float *st, int k, unsigned tp,
-                                                      const RecEntry *rec) {
+                                                      unsigned so, uint16_t *pk, int k,
+                                                      unsigned tp, const RecEntry *rec) {
         constexpr int Q8 = (RQ + 8) % 9, Q4 = (RQ + 4) % 9;
         constexpr int SA_OWN = (RQ + 8) % NA, SA_HALO = (RQ + 4) % NA, SB = RQ % NB;
         // fill parities: relative plane r + 8 fills slot SA_OWN for the
         // (trip + (RQ + 8) / 9)-th time; plane r fills SB for the (3 trip + RQ / 3)-th
         constexpr unsigned PA = ((RQ + 8) / NA) & 1u, PB = (RQ / NB) & 1u;
+        constexpr int OA_OWN = SA_OWN * Cfg::kSlotABytes, OA_HALO = SA_HALO * Cfg::kSlotABytes;
+        constexpr int OB = SB * Cfg::kSlotBBytes;
+        constexpr int RA = Cfg::kRowW * 2, RB = TX * 2, WB = Cfg::kTile * 2, RS = Cfg::kSW * 4;
         const int r = k - cx.z0;
 
-        // plane k + 4 of this thread's two rows -> the queue (decoded once)
-        wk.ok = wait_phase(&br.fullA[SA_OWN], tp ^ PA, &br.abort, a.status) && wk.ok;
-        {
-            const uint16_t *p = cx.ringA + SA_OWN * Cfg::kSlotA + cx.offA;
-            wk.q[Q8][0] = Fmt::decode(lds2u(p));
-            wk.q[Q8][1] = Fmt::decode(lds2u(p + Cfg::kRowW));
-        }
+        // U of plane k + 4 (ring A) and D, W of plane k (ring B): one test of
+        // both barriers, the bounded waits only when either is not complete
+        if (!(mbar_try_wait(&br.fullA[SA_OWN], tp ^ PA) & mbar_try_wait(&br.fullB[SB], tp ^ PB)))
+            wk.ok = wait_phase(&br.fullA[SA_OWN], tp ^ PA, &br.abort, a.status) &&
+                    wait_phase(&br.fullB[SB], tp ^ PB, &br.abort, a.status) && wk.ok;
+        // this thread's two rows of plane k + 4 -> the queue (decoded once)
+        wk.q[Q8][0] = Fmt::decode(lds2_at<OA_OWN>(cx.aOwn));
+        wk.q[Q8][1] = Fmt::decode(lds2_at<OA_OWN + RA>(cx.aOwn));
         // D and W of plane k (raw; decoded where they are used)
-        wk.ok = wait_phase(&br.fullB[SB], tp ^ PB, &br.abort, a.status) && wk.ok;
-        const uint16_t *tb = cx.ringB + SB * Cfg::kSlotB + cx.offB;
-        const uint2 dr0 = lds2u(tb), dr1 = lds2u(tb + TX);
-        const uint2 wr0 = lds2u(tb + Cfg::kTile), wr1 = lds2u(tb + Cfg::kTile + TX);
-        const float gzk = __ldg(cx.gz + k);
+        const uint2 dr0 = lds2_at<OB>(cx.bOwn), dr1 = lds2_at<OB + RB>(cx.bOwn);
+        const uint2 wr0 = lds2_at<OB + WB>(cx.bOwn), wr1 = lds2_at<OB + WB + RB>(cx.bOwn);
 
         // staging tile of plane k: this thread's own two rows (decoded four
         // planes ago) and its halo unit; then every thread agrees before
         // anyone reads a neighbour
-        sts4(st + cx.offS, wk.q[Q4][0]);
-        sts4(st + cx.offS + Cfg::kSW, wk.q[Q4][1]);
-        {
-            const uint16_t *src = cx.ringA + SA_HALO * Cfg::kSlotA;
-            sts4(st + cx.band_dst, Fmt::decode(lds2u(src + cx.band_src)));
-            if (cx.side) sts4(st + cx.side_dst, Fmt::decode(lds2u(src + cx.side_src)));
-        }
+        const unsigned st = cx.sOwn + so;
+        sts4_at<0>(st, wk.q[Q4][0]);
+        sts4_at<RS>(st, wk.q[Q4][1]);
+        if (Cfg::kAllFirst || cx.unit1)
+            sts4_at<0>(cx.sUnit1 + so, Fmt::decode(lds2_at<OA_HALO>(cx.aUnit1)));
+        if (Cfg::kSecond && cx.unit2)
+            sts4_at<0>(cx.sUnit2 + so, Fmt::decode(lds2_at<OA_HALO>(cx.aUnit2)));
         wk.ok = __syncthreads_and(wk.ok) != 0;
         if (!wk.ok) return;
         // every thread is done with ring-A slot SA_HALO (plane k) and ring-B
         // slot SB: refill them with planes k + 9 (U) and k + 3 (D, W)
-        if (threadIdx.x == 0 && r + 4 + NA < cx.nplanes)
-            issue_a(br, ringA_w, mp, it, SA_HALO, r + 4 + NA);
-        if (threadIdx.x == 32 && r + NB < cx.nb) issue_b(br, ringB_w, mp, it, SB, r + NB);
-
-        const float *row = st + cx.offS;
-        const float4 xl0 = lds4(row - 4), xr0 = lds4(row + 4);
-        const float4 xl1 = lds4(row + Cfg::kSW - 4), xr1 = lds4(row + Cfg::kSW + 4);
-        // rows j-4..j-1 and j+2..j+5
-        float4 lm[4], lp[4];
-#pragma unroll
-        for (int m = 1; m <= 4; ++m) {
-            lm[m - 1] = lds4(row - m * Cfg::kSW);
-            lp[m - 1] = lds4(row + (m + 1) * Cfg::kSW);
+        if (threadIdx.x == 0) {
+            if (r + 4 + NA < cx.nplanes) issue_a(br, ringA, mp, it, SA_HALO, r + 4 + NA);
+            if (r + NB < cx.nb) issue_b(br, ringB, mp, it, SB, r + NB);
         }
+
+        const float4 xl0 = lds4_at<-16>(st), xr0 = lds4_at<16>(st);
+        const float4 xl1 = lds4_at<RS - 16>(st), xr1 = lds4_at<RS + 16>(st);
+        // rows j-4..j-1 and j+2..j+5
+        const float4 lm[4] = {lds4_at<-RS>(st), lds4_at<-2 * RS>(st), lds4_at<-3 * RS>(st),
+                              lds4_at<-4 * RS>(st)};
+        const float4 lp[4] = {lds4_at<2 * RS>(st), lds4_at<3 * RS>(st), lds4_at<4 * RS>(st),
+                              lds4_at<5 * RS>(st)};
         float2 lap0[2], lap1[2];
         {
             const float4 yp[4] = {wk.q[Q4][1], lp[0], lp[1], lp[2]};
-            stencil_row<RQ>(wk, 0, xl0, xr0, yp, lm, fc, lap0);
+            stencil_row<RQ>(wk, 0, xl0, xr0, yp, lm, lap0);
         }
         {
             const float4 ym[4] = {wk.q[Q4][0], lm[0], lm[1], lm[2]};
-            stencil_row<RQ>(wk, 1, xl1, xr1, lp, ym, fc, lap1);
+            stencil_row<RQ>(wk, 1, xl1, xr1, lp, ym, lap1);
         }
         const float4 d0 = Fmt::decode(dr0), d1 = Fmt::decode(dr1);
         const float4 w0 = Fp16Fmt::decode(wr0), w1 = Fp16Fmt::decode(wr1);
+        // the common plane: taper 1 everywhere in the tile, no source, no
+        // receiver, no change of scale, every cell inside the grid
+        if (cx.lean && (unsigned)(k - cx.fz0) < (unsigned)(cx.fz1 - cx.fz0) && k != wk.rnext_k) {
+            const float4 dn0 = delta_fast(lap0, d0, w0), dn1 = delta_fast(lap1, d1, w1);
+            const float4 un0 = add4(wk.q[Q4][0], dn0), un1 = add4(wk.q[Q4][1], dn1);
+            const uint2 su0 = Fmt::encode(un0), su1 = Fmt::encode(un1);
+            const uint2 sd0 = Fmt::encode(dn0), sd1 = Fmt::encode(dn1);
+            uint16_t *pd = pk + cx.d_delta;
+            store16(pk, su0);
+            store16(pd, sd0);
+            store16(pk + cx.pitch, su1);
+            store16(pd + cx.pitch, sd1);
+            wk.amax = Fmt::amax(Fmt::amax(wk.amax, su0.x), su0.y);
+            wk.amax = Fmt::amax(Fmt::amax(wk.amax, su1.x), su1.y);
+            return;
+        }
         float4 dn[2];
         if (cx.xy_free && k >= cx.fz0 && k < cx.fz1) {
             dn[0] = delta_fast(lap0, d0, w0);
             dn[1] = delta_fast(lap1, d1, w1);
         } else {
+            const float gzk = __ldg(cx.gz + k);
             dn[0] = delta_taper(lap0, d0, w0, wk.q[Q4][0], cx.gxy[0], gzk);
             dn[1] = delta_taper(lap1, d1, w1, wk.q[Q4][1], cx.gxy[1], gzk);
         }
@@ -519,13 +585,7 @@ struct Kern16 {
             const float4 w[2] = {w0, w1};
             inject_sources(dn, w, cx.src_mask, a.src, cx.i, cx.j, k, fc.wtrue, fc.amp2r);
         }
-        float4 un[2];
-#pragma unroll
-        for (int rr = 0; rr < 2; ++rr) {
-            const float2 a0 = add2(lo2(wk.q[Q4][rr]), lo2(dn[rr]));
-            const float2 a1 = add2(hi2(wk.q[Q4][rr]), hi2(dn[rr]));
-            un[rr] = make_float4(a0.x, a0.y, a1.x, a1.y);
-        }
+        float4 un[2] = {add4(wk.q[Q4][0], dn[0]), add4(wk.q[Q4][1], dn[1])};
         if (k == wk.rnext_k) {
             const int2 rc = record16(un[0], un[1], fc.r2t, k, wk.rcur, wk.rend, rec, a.traces,
                                      a.nt_max, a.trace_step);
@@ -535,64 +595,56 @@ struct Kern16 {
         if (fc.ro != 1.0f) {   // the output exponent differs from the input's (rare)
 #pragma unroll
             for (int rr = 0; rr < 2; ++rr) {
-                const float2 a0 = mul2(lo2(un[rr]), splat(fc.ro)), a1 = mul2(hi2(un[rr]), splat(fc.ro));
-                const float2 b0 = mul2(lo2(dn[rr]), splat(fc.ro)), b1 = mul2(hi2(dn[rr]), splat(fc.ro));
-                un[rr] = make_float4(a0.x, a0.y, a1.x, a1.y);
-                dn[rr] = make_float4(b0.x, b0.y, b1.x, b1.y);
+                un[rr] = mul4(un[rr], fc.ro);
+                dn[rr] = mul4(dn[rr], fc.ro);
             }
         }
-        uint2 su[2], sd[2];
-#pragma unroll
-        for (int rr = 0; rr < 2; ++rr) {
-            su[rr] = Fmt::encode(un[rr]);
-            sd[rr] = Fmt::encode(dn[rr]);
-        }
-        uint16_t *pk = cx.pu + (long long)r * cx.plane;
+        const uint2 su0 = Fmt::encode(un[0]), su1 = Fmt::encode(un[1]);
+        const uint2 sd0 = Fmt::encode(dn[0]), sd1 = Fmt::encode(dn[1]);
         if (cx.full) {
-            store16(pk, su[0]);
-            store16(pk + cx.d_delta, sd[0]);
-            store16(pk + cx.pitch, su[1]);
-            store16(pk + cx.pitch + cx.d_delta, sd[1]);
+            uint16_t *pd = pk + cx.d_delta;
+            store16(pk, su0);
+            store16(pd, sd0);
+            store16(pk + cx.pitch, su1);
+            store16(pd + cx.pitch, sd1);
         } else if (cx.nvalid > 0) {
-            store_partial(pk, cx.d_delta, cx.pitch, su[0], sd[0], su[1], sd[1], cx.nvalid, cx.row1);
+            store_partial(pk, cx.d_delta, cx.pitch, su0, sd0, su1, sd1, cx.nvalid, cx.row1);
         }
         // cells outside the grid have zero taper, so zero u~ (NaN canaries in
         // the padding are ignored by the max)
-        wk.amax = Fmt::amax(wk.amax, su[0].x);
-        wk.amax = Fmt::amax(wk.amax, su[0].y);
-        wk.amax = Fmt::amax(wk.amax, su[1].x);
-        wk.amax = Fmt::amax(wk.amax, su[1].y);
+        wk.amax = Fmt::amax(Fmt::amax(wk.amax, su0.x), su0.y);
+        wk.amax = Fmt::amax(Fmt::amax(wk.amax, su1.x), su1.y);
     }
 
-    // planes kb + RQ .. kb + NA - 1 of a trip; false once the item ends
+    // planes kb + RQ .. kb + NA - 1 of a trip; false once the item ends.
+    // se / so: staging byte offsets of even / odd RQ; pk: U' of (i, j, kb)
     template <int RQ>
     static __device__ __forceinline__ bool planes(Walk16 &wk, const Ctx16 &cx, B &br,
-                                                  uint16_t *ringA_w, uint16_t *ringB_w,
+                                                  uint16_t *ringA, uint16_t *ringB,
                                                   const Maps16 &mp, const Item &it,
                                                   const StepArgs &a, const Factors &fc,
-                                                  float *st_even, float *st_odd, int kb,
+                                                  unsigned se, unsigned so, uint16_t *pk, int kb,
                                                   unsigned tp, const RecEntry *rec) {
         if constexpr (RQ < NA) {
             if (kb + RQ >= cx.z1) return false;
-            plane_step<RQ>(wk, cx, br, ringA_w, ringB_w, mp, it, a, fc,
-                           (RQ & 1) ? st_odd : st_even, kb + RQ, tp, rec);
+            plane_step<RQ>(wk, cx, br, ringA, ringB, mp, it, a, fc, (RQ & 1) ? so : se, pk,
+                           kb + RQ, tp, rec);
             // wk.ok is the same in every thread after the plane barrier
             if (!wk.ok) return false;
-            return planes<RQ + 1>(wk, cx, br, ringA_w, ringB_w, mp, it, a, fc, st_even, st_odd,
-                                  kb, tp, rec);
+            return planes<RQ + 1>(wk, cx, br, ringA, ringB, mp, it, a, fc, se, so,
+                                  pk + cx.plane, kb, tp, rec);
         }
         return true;
     }
 };
 
 template <class Fmt, int TX, int TY, int NA, int NB>
-__global__ void __launch_bounds__(Cfg16<TX, TY, NA, NB>::kThreads, 3)
-    step_stream16_kernel(const __grid_constant__ Maps16 maps, uint16_t *__restrict__ u_out,
-                         uint16_t *d_io, const __grid_constant__ StepArgs a,
+__global__ void __launch_bounds__(Cfg16<TX, TY, NA, NB>::kThreads, Cfg16<TX, TY, NA, NB>::kMinBlocks)
+    step_stream16_kernel(const __grid_constant__ Maps16 maps, uint16_t *u_out, uint16_t *d_io,
+                         const __grid_constant__ StepArgs a,
                          Scale16 *__restrict__ sc, const long long step, const float src_hint,
-                         const Weights16 wt, const Free16 fr, const int zb, const int tiles_x,
-                         const int ntiles, const int *__restrict__ rec_ptr,
-                         const RecEntry *__restrict__ rec) {
+                         const Free16 fr, const int zb, const int tiles_x, const int ntiles,
+                         const int *__restrict__ rec_ptr, const RecEntry *__restrict__ rec) {
     using K = Kern16<Fmt, TX, TY, NA, NB>;
     using Cfg = typename K::Cfg;
     extern __shared__ __align__(128) float smem16[];
@@ -608,11 +660,6 @@ __global__ void __launch_bounds__(Cfg16<TX, TY, NA, NB>::kThreads, 3)
     const int e = sc->e[sn];
     const int e_o = scale_exponent(fmaxf(__uint_as_float(sc->amax[sn]), src_hint));
     typename K::Factors fc;
-    fc.c0 = wt.c0;
-    fc.c1 = wt.c1;
-    fc.c2 = wt.c2;
-    fc.c3 = wt.c3;
-    fc.c4 = wt.c4;
     fc.wtrue = pow2f(-kW16Exp);
     fc.amp2r = scale2(1.0f, e);
     fc.ro = pow2f(e_o - e);
@@ -644,37 +691,43 @@ __global__ void __launch_bounds__(Cfg16<TX, TY, NA, NB>::kThreads, 3)
         for (int pr = 0; pr < NA && pr < nplanes; ++pr)
             if (!(pr == 0 && stall))   // test hook: never filled, the bounded waits run out
                 K::issue_a(br, ringA, maps, it, pr, pr);
-    }
-    if (tid == 32) {
         for (int b = 0; b < NB && b < nb; ++b) K::issue_b(br, ringB, maps, it, b, b);
     }
 
     Ctx16 cx;
     const int tx = tid % Cfg::kCols, py = tid / Cfg::kCols;
-    cx.ringA = ringA;
-    cx.ringB = ringB;
-    cx.stage = stage;
     cx.i = it.i0 + 4 * tx;
     cx.j = it.j0 + 2 * py;
     cx.z0 = it.z0;
     cx.z1 = it.z1;
     cx.nb = nb;
     cx.nplanes = nplanes;
-    cx.offA = (kHalo + 2 * py) * Cfg::kRowW + Cfg::kLead + 4 * tx;
-    cx.offB = 2 * py * TX + 4 * tx;
-    cx.offS = (kHalo + 2 * py) * Cfg::kSW + kHalo + 4 * tx;
     {
-        const int band = tid / Cfg::kCols, n = tid - band * Cfg::kCols;
-        int y = band < kHalo ? band : TY + band;            // rows 0..3, TY+4..TY+7
-        int c = kHalo + 4 * n;                                // staging column
-        cx.band_src = y * Cfg::kRowW + c + (Cfg::kLead - kHalo);
-        cx.band_dst = y * Cfg::kSW + c;
-        const int v = tid & 31;
-        y = kHalo + (v >> 1);
-        c = (v & 1) ? TX + kHalo : 0;
-        cx.side_src = y * Cfg::kRowW + c + (Cfg::kLead - kHalo);
-        cx.side_dst = y * Cfg::kSW + c;
-        cx.side = (tid >> 5) == Cfg::kSideWarp;
+        const unsigned rA = smem_addr(ringA), rB = smem_addr(ringB), st0 = smem_addr(stage);
+        cx.aOwn = rA + 2u * ((kHalo + 2 * py) * Cfg::kRowW + Cfg::kLead + 4 * tx);
+        cx.bOwn = rB + 2u * (2 * py * TX + 4 * tx);
+        cx.sOwn = st0 + 4u * ((kHalo + 2 * py) * Cfg::kSW + kHalo + 4 * tx);
+        // halo unit u: u < 2 TX, 4 cells above/below the tile (rows 0..3,
+        // TY+4..TY+7 of the staging tile); else 4 cells left/right of row
+        // (u - 2 TX) / 2. Source and destination offsets of unit u:
+        auto unit = [&](int u, unsigned *a, unsigned *s) {
+            int y, c;
+            if (u < Cfg::kBandUnits) {
+                const int band = u / Cfg::kCols;
+                y = band < kHalo ? band : TY + band;
+                c = kHalo + 4 * (u - band * Cfg::kCols);
+            } else {
+                const int v = u - Cfg::kBandUnits;
+                y = kHalo + (v >> 1);
+                c = (v & 1) ? TX + kHalo : 0;
+            }
+            *a = rA + 2u * (y * Cfg::kRowW + c + (Cfg::kLead - kHalo));
+            *s = st0 + 4u * (y * Cfg::kSW + c);
+        };
+        cx.unit1 = tid < Cfg::kUnits;
+        cx.unit2 = tid + Cfg::kThreads < Cfg::kUnits;
+        unit(cx.unit1 ? tid : 0, &cx.aUnit1, &cx.sUnit1);
+        unit(cx.unit2 ? tid + Cfg::kThreads : 0, &cx.aUnit2, &cx.sUnit2);
     }
     const bool col_ok = (cx.j < g.ny) && (cx.i < g.nx);
     cx.nvalid = col_ok ? min(4, g.nx - cx.i) : 0;
@@ -683,7 +736,7 @@ __global__ void __launch_bounds__(Cfg16<TX, TY, NA, NB>::kThreads, 3)
     cx.pitch = g.pnx;
     cx.plane = g.plane;
     cx.d_delta = d_io - u_out;
-    cx.pu = u_out + pidx(g, col_ok ? cx.i : 0, col_ok ? cx.j : 0, it.z0);
+    uint16_t *pu = u_out + pidx(g, col_ok ? cx.i : 0, col_ok ? cx.j : 0, it.z0);
     cx.gz = a.gz;
     cx.fz0 = fr.z0;
     cx.fz1 = fr.z1;
@@ -706,6 +759,7 @@ __global__ void __launch_bounds__(Cfg16<TX, TY, NA, NB>::kThreads, 3)
             ss.k >= it.z0 && ss.k < it.z1)
             cx.src_mask |= 1u << qs;
     }
+    cx.lean = cx.xy_free && cx.src_mask == 0u && fc.ro == 1.0f;
 
     Walk16 wk;
     wk.ok = true;
@@ -722,7 +776,7 @@ __global__ void __launch_bounds__(Cfg16<TX, TY, NA, NB>::kThreads, 3)
 #pragma unroll
     for (int m = 0; m < 2 * kHalo; ++m) {
         wk.ok = wk.ok && wait_phase(&br.fullA[m], 0u, &br.abort, a.status);
-        const uint16_t *p = ringA + m * Cfg::kSlotA + cx.offA;
+        const uint16_t *p = ringA + m * Cfg::kSlotA + (cx.aOwn - smem_addr(ringA)) / 2;
         wk.q[m][0] = Fmt::decode(lds2u(p));
         wk.q[m][1] = Fmt::decode(lds2u(p + Cfg::kRowW));
     }
@@ -734,10 +788,10 @@ __global__ void __launch_bounds__(Cfg16<TX, TY, NA, NB>::kThreads, 3)
                 K::issue_a(br, ringA, maps, it, pr - NA, pr);
         unsigned tp = 0;
         for (int kb = it.z0;; kb += NA, tp ^= 1u) {
-            float *st_even = stage + (kb & 1) * Cfg::kStage;
-            float *st_odd = stage + ((kb + 1) & 1) * Cfg::kStage;
-            if (!K::template planes<0>(wk, cx, br, ringA, ringB, maps, it, a, fc, st_even, st_odd,
-                                       kb, tp, rec))
+            // staging buffer of plane k: k & 1
+            const unsigned se = (kb & 1) * Cfg::kStageBytes, sodd = Cfg::kStageBytes - se;
+            if (!K::template planes<0>(wk, cx, br, ringA, ringB, maps, it, a, fc, se, sodd,
+                                       pu + (long long)(kb - it.z0) * cx.plane, kb, tp, rec))
                 break;
         }
     }
@@ -762,14 +816,12 @@ __global__ void __launch_bounds__(Cfg16<TX, TY, NA, NB>::kThreads, 3)
     }
 }
 
+// Resident CTAs per SM and SM count of one instantiation on the current
+// device, looked up (and its shared-memory limit set) the first time.
 template <class Fmt, int TX, int TY, int NA, int NB>
-cudaError_t launch16(const Maps16 &maps, uint16_t *u_out, uint16_t *d_io, const StepArgs &a,
-                     Scale16 *sc, long long step, float src_hint, const Weights16 &wt,
-                     const Free16 &fr, int zb, const int *rec_ptr, const RecEntry *rec,
-                     cudaStream_t s) {
+cudaError_t facts16(int *ctas, int *sms) {
     using Cfg = Cfg16<TX, TY, NA, NB>;
     auto kern = step_stream16_kernel<Fmt, TX, TY, NA, NB>;
-    // the shared-memory limit is a per-device property of the kernel
     static LaunchFacts lf;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -778,24 +830,52 @@ cudaError_t launch16(const Maps16 &maps, uint16_t *u_out, uint16_t *d_io, const 
     if (lf.ctas[dev] == 0) {
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)Cfg::kSmem);
-        int c = 0;
+        int c = 0, n = 0;
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
         if (e == cudaSuccess)
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, kern, Cfg::kThreads, Cfg::kSmem);
         if (e != cudaSuccess) return e;
         if (c < 1) return cudaErrorInvalidConfiguration;
+        lf.sms[dev] = n;
         lf.ctas[dev] = c;
     }
+    *ctas = lf.ctas[dev];
+    *sms = lf.sms[dev];
+    return cudaSuccess;
+}
+
+template <class Fmt, int TX, int TY, int NA, int NB>
+cudaError_t launch16(const Maps16 &maps, uint16_t *u_out, uint16_t *d_io, const StepArgs &a,
+                     Scale16 *sc, long long step, float src_hint, const Free16 &fr, int zb,
+                     const int *rec_ptr, const RecEntry *rec, cudaStream_t s) {
+    using Cfg = Cfg16<TX, TY, NA, NB>;
+    auto kern = step_stream16_kernel<Fmt, TX, TY, NA, NB>;
+    int ctas = 0, sms = 0;
+    cudaError_t e = facts16<Fmt, TX, TY, NA, NB>(&ctas, &sms);
+    if (e != cudaSuccess) return e;
     const int tiles_x = (a.g.nx + TX - 1) / TX;
     const int ntiles = tiles_x * ((a.g.ny + TY - 1) / TY);
     const int nitems = ntiles * ((a.g.nz + zb - 1) / zb);
-    kern<<<nitems, Cfg::kThreads, Cfg::kSmem, s>>>(maps, u_out, d_io, a, sc, step, src_hint, wt,
-                                                   fr, zb, tiles_x, ntiles, rec_ptr, rec);
+    kern<<<nitems, Cfg::kThreads, Cfg::kSmem, s>>>(maps, u_out, d_io, a, sc, step, src_hint, fr,
+                                                   zb, tiles_x, ntiles, rec_ptr, rec);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-bool stream16_tiling_supported(int tx, int ty) { return tx == 64 && ty == 16; }
+bool stream16_tiling_supported(int tx, int ty) {
+    return tx == 64 && (ty == 16 || ty == 24 || ty == 48);
+}
+
+cudaError_t stream16_slots(int ty, int *slots) {
+    int c = 0, n = 0;
+    cudaError_t e = cudaErrorInvalidValue;
+    if (ty == 16) e = facts16<Fp16Fmt, 64, 16, 9, 3>(&c, &n);
+    if (ty == 24) e = facts16<Fp16Fmt, 64, 24, 9, 3>(&c, &n);
+    if (ty == 48) e = facts16<Fp16Fmt, 64, 48, 9, 3>(&c, &n);
+    if (e == cudaSuccess) *slots = c * n;
+    return e;
+}
 
 // Weights of the 16-bit kernel, times 2^-kW16Exp: floats within 7e-7 of the
 // Taylor weights, chosen so that c0 = -6 (c1 + c2 + c3 + c4) holds exactly.
@@ -818,24 +898,38 @@ Weights16 zero_sum_weights16() {
                      (float)(c4 * f)};
 }
 
-cudaError_t launch_step_stream16(int storage, const CUtensorMap *tmap_u, const CUtensorMap *tmap_d,
-                                 const CUtensorMap *tmap_w, uint16_t *u_out, uint16_t *d_io,
-                                 const StepArgs &a, Scale16 *sc, long long step, float src_hint,
-                                 const Free16 &fr, const StreamTiling &t, const int *rec_ptr,
-                                 const RecEntry *rec, cudaStream_t s) {
-    static const Weights16 wt = zero_sum_weights16();
-    if (!(t.tx == 64 && t.ty == 16)) return cudaErrorInvalidValue;
+cudaError_t launch_step_stream16(int storage, const Maps16In &m, const StepArgs &a, Scale16 *sc,
+                                 long long step, float src_hint, const Free16 &fr,
+                                 const StreamTiling &t, const int *rec_ptr, const RecEntry *rec,
+                                 cudaStream_t s) {
+    // the kernel's compile-time weights must be those of zero_sum_weights16
+    static const bool weights_ok = [] {
+        const Weights16 w = zero_sum_weights16();
+        return w.c0 == kW16C0 && w.c1 == kW16C1 && w.c2 == kW16C2 && w.c3 == kW16C3 &&
+               w.c4 == kW16C4;
+    }();
+    if (!weights_ok) return cudaErrorInvalidValue;
+    if (!stream16_tiling_supported(t.tx, t.ty)) return cudaErrorInvalidValue;
     Maps16 maps;
-    maps.u = *tmap_u;
-    maps.d = *tmap_d;
-    maps.w = *tmap_w;
-    // ring A 9 slots (the planes of one loop trip), ring B 3, 3 CTAs per SM
-    if (storage == WS_STORAGE_BF16)
-        return launch16<Bf16Fmt, 64, 16, 9, 3>(maps, u_out, d_io, a, sc, step, src_hint, wt, fr,
-                                                t.zb, rec_ptr, rec, s);
-    if (storage == WS_STORAGE_FP16)
-        return launch16<Fp16Fmt, 64, 16, 9, 3>(maps, u_out, d_io, a, sc, step, src_hint, wt, fr,
-                                                t.zb, rec_ptr, rec, s);
+    maps.u = *m.u;
+    maps.d = *m.d;
+    maps.w = *m.w;
+    // ring A 9 slots (the planes of one loop trip), ring B 3; 64 x 16 tiles
+    // run 3 CTAs per SM, 64 x 24 two, 64 x 48 one (12 warps in all)
+#define WS_LAUNCH16(FMT, TY)                                                                     \
+    return launch16<FMT, 64, TY, 9, 3>(maps, m.u_out, m.d_io, a, sc, step, src_hint, fr, t.zb, \
+                                       rec_ptr, rec, s)
+    if (storage == WS_STORAGE_BF16) {
+        if (t.ty == 16) WS_LAUNCH16(Bf16Fmt, 16);
+        if (t.ty == 24) WS_LAUNCH16(Bf16Fmt, 24);
+        if (t.ty == 48) WS_LAUNCH16(Bf16Fmt, 48);
+    }
+    if (storage == WS_STORAGE_FP16) {
+        if (t.ty == 16) WS_LAUNCH16(Fp16Fmt, 16);
+        if (t.ty == 24) WS_LAUNCH16(Fp16Fmt, 24);
+        if (t.ty == 48) WS_LAUNCH16(Fp16Fmt, 48);
+    }
+#undef WS_LAUNCH16
     return cudaErrorInvalidValue;
 }
 

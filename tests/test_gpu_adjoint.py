@@ -263,3 +263,72 @@ def test_forward_then_residual_gradient_reuses_the_run():
     _, g_ref, _ = _gpu((vel * 1.01).astype(np.float32), h, dt, nt, src, rec, sponge, r,
                        mode=wsb.WS_ADJ_RESIDUAL)
     np.testing.assert_array_equal(g_new, g_ref)
+
+
+def test_several_shots_sum_and_norm_against_oracle():
+    """ws_adjoint_gradient_shots: three shots on one model (each its own
+    sources, receivers and stream) against the FP64 oracle's summed adjoint
+    gradient, with the same seeded residuals; the summed misfit; the FP64
+    gradient norm against the norm of the oracle's gradient; and each shot
+    alone through ws_adjoint_gradient gives the same summed field."""
+    torch = pytest.importorskip("torch")
+    nx, ny, nz, nt = 150, 40, 36, 64
+    vel, h, dt, _, _, sponge, _ = _case(nx, ny, nz, nt)
+    v64 = vel.astype(np.float64)
+    rng = np.random.default_rng(31)
+    shots = []
+    for q in range(3):
+        src = [(20 + 50 * q, 10 + 9 * q, 3 + q, 25.0 + 2 * q, 0.04, 1.0 - 0.3 * q)]
+        cells = rng.choice(nx * ny * nz, 9 + q, replace=False)
+        rec = np.stack([cells % nx, cells // nx % ny, cells // (nx * ny)], axis=1).astype(np.int32)
+        tr = oracle.run(v64, h, dt, nt, sources=src, receivers=rec, sponge=sponge)["traces"]
+        r = rng.standard_normal(tr.shape).astype(np.float32)
+        ref = oracle.adjoint_gradient(v64, h, dt, nt, tr - r.astype(np.float64), sources=src,
+                                      receivers=rec, sponge=sponge)
+        shots.append((src, rec, r, ref))
+    g_ref = sum(s[3]["grad_m"] for s in shots)
+    j_ref = sum(s[3]["misfit"] for s in shots)
+
+    handles, streams = [], []
+    for src, rec, _, _ in shots:
+        hd = wsb.ws_create(nx, ny, nz, h, dt)
+        st = torch.cuda.Stream()
+        wsb.ws_set_stream(hd, st)
+        wsb.ws_set_velocity(hd, vel)
+        wsb.ws_set_sponge(hd, *sponge)
+        for s in src:
+            wsb.ws_add_source(hd, *s)
+        wsb.ws_set_receivers(hd, rec, nt)
+        handles.append(hd)
+        streams.append(st)
+    g, j, gn = wsb.ws_adjoint_gradient_shots(handles, [s[2] for s in shots], wsb.WS_ADJ_RESIDUAL)
+    err = _rel(g, g_ref)
+    print(f"3 shots: summed gradient max error / max |g| = {err:.2e}, norm {gn:.6e} vs "
+          f"{np.linalg.norm(g_ref):.6e}")
+    assert err <= TOL, err
+    assert j == pytest.approx(j_ref, rel=1e-6)
+    # the norm is the FP64 norm of the returned field, and close to the oracle's
+    assert gn == pytest.approx(np.linalg.norm(g.astype(np.float64)), rel=1e-12)
+    assert gn == pytest.approx(np.linalg.norm(g_ref), rel=TOL)
+    # shot by shot through the single-shot call: the same per-shot fields,
+    # summed here in FP64 in shot order
+    acc = np.zeros((nz, ny, nx))
+    for hd, (_, _, r, _) in zip(handles, shots):
+        gq, _ = wsb.ws_adjoint_gradient(hd, r, wsb.WS_ADJ_RESIDUAL)
+        acc += gq.astype(np.float64)
+    np.testing.assert_array_equal(g, acc.astype(np.float32))
+
+
+def test_several_shots_reject_mismatched_handles():
+    a = wsb.ws_create(40, 20, 16, 10.0, 1e-3)
+    b = wsb.ws_create(40, 20, 17, 10.0, 1e-3)
+    d = np.zeros((1, 4), np.float32)
+    for h in (a, b):
+        wsb.ws_set_velocity(h, np.full(h.shape, 2000.0, np.float32))
+        wsb.ws_set_receivers(h, np.array([[1, 1, 1]], np.int32), 4)
+    with pytest.raises(wsb.WaveStepError) as e:
+        wsb.ws_adjoint_gradient_shots([a, b], [d, d])
+    assert e.value.code == wsb.WS_ERR_BADARG
+    with pytest.raises(wsb.WaveStepError) as e:
+        wsb.ws_adjoint_gradient_shots([a, a], [d, d])
+    assert e.value.code == wsb.WS_ERR_BADARG

@@ -54,6 +54,7 @@ CASES = [
     (wsb.WS_STORAGE_FP32, wsb.WS_KERNEL_DIRECT, (0, 0)),
     (wsb.WS_STORAGE_FP16, wsb.WS_KERNEL_STREAM, (0, 0)),
     (wsb.WS_STORAGE_BF16, wsb.WS_KERNEL_STREAM, (0, 0)),
+    (wsb.WS_STORAGE_FP16, wsb.WS_KERNEL_STREAM, (64, 16)),
 ]
 
 

@@ -62,9 +62,10 @@ def ulp_fp16(x, e=0):
     return np.ldexp(1.0, np.maximum(k - 11, -24) - e)
 
 
-@pytest.mark.parametrize("shape", [(200, 60, 30), (99, 37, 21)])   # taper-free tiles; ragged x, odd y
+@pytest.mark.parametrize("tile_y", [16, 24, 48])
+@pytest.mark.parametrize("shape", [(200, 60, 30), (99, 57, 21)])   # taper-free tiles; ragged x, odd y
 @pytest.mark.parametrize("storage,name", MODES)
-def test_one_step_is_the_rounded_exact_update(storage, name, shape):
+def test_one_step_is_the_rounded_exact_update(storage, name, shape, tile_y):
     nx, ny, nz = shape
     h, v = 10.0, 2000.0
     dt = 0.25 * h / v                      # (V dt / h)^2 = 1/16, exact everywhere
@@ -85,6 +86,7 @@ def test_one_step_is_the_rounded_exact_update(storage, name, shape):
     sponge = (5, 0.1)
 
     hd = wsb.ws_create(nx, ny, nz, h, dt)
+    wsb.ws_set_kernel(hd, wsb.WS_KERNEL_AUTO, 64, tile_y, 0)
     wsb.ws_set_storage(hd, storage)
     wsb.ws_set_velocity(hd, vel)
     wsb.ws_set_sponge(hd, *sponge)
@@ -192,17 +194,21 @@ def test_storage_modes_against_oracle_to_1000_steps():
         wsb.ws_destroy(hd)
 
 
-@pytest.mark.parametrize("shape", [(64, 16, 1), (64, 16, 3), (70, 17, 6), (128, 16, 2)])
+@pytest.mark.parametrize("shape", [(64, 16, 1), (64, 16, 3), (70, 17, 6), (128, 16, 2),
+                                   (64, 24, 2), (70, 25, 5), (65, 48, 3), (130, 50, 4)])
 @pytest.mark.parametrize("storage,name", MODES)
 def test_thin_and_minimal_grids(storage, name, shape):
     """The smallest grids 16-bit storage accepts (nx >= 64, ny >= 16), down to
-    one plane, ragged in x and y: 30 steps against the FP64 oracle."""
+    one plane, ragged in x and y, with each tile height that fits the grid
+    (64 x 16 from ny = 16, 64 x 24 from 24, 64 x 48 from 48): 30 steps against
+    the FP64 oracle."""
     nx, ny, nz = shape
     vel = synthetic.smooth_random_velocity((nz, ny, nx), 11, spacing=4)
     h, dt = 10.0, synthetic.cfl_dt(4500.0, 10.0)
     src = [(nx // 3, ny // 2, nz // 2, 20.0, 0.04, 1.0)]
     rec = np.array([[0, 0, 0], [nx - 1, ny - 1, nz - 1], [nx // 2, ny // 3, nz // 2]], np.int32)
     hd = wsb.ws_create(nx, ny, nz, h, dt)
+    wsb.ws_set_kernel(hd, wsb.WS_KERNEL_AUTO, 64, max(t for t in (16, 24, 48) if t <= ny), 0)
     wsb.ws_set_storage(hd, storage)
     wsb.ws_set_velocity(hd, vel)
     wsb.ws_set_sponge(hd, 3, 0.1)
@@ -248,6 +254,13 @@ def test_storage_needs_a_64_wide_grid():
     hd = wsb.ws_create(48, 16, 16, 10.0, 1e-3)
     with pytest.raises(wsb.WaveStepError) as e:
         wsb.ws_set_storage(hd, wsb.WS_STORAGE_BF16)
+    assert e.value.code == wsb.WS_ERR_BADARG
+    hd = wsb.ws_create(64, 30, 16, 10.0, 1e-3)       # a 16-bit tile taller than the grid
+    with pytest.raises(wsb.WaveStepError) as e:
+        wsb.ws_set_kernel(hd, wsb.WS_KERNEL_AUTO, 64, 48, 0)
+    assert e.value.code == wsb.WS_ERR_BADARG
+    with pytest.raises(wsb.WaveStepError) as e:      # not a tile of either streaming kernel
+        wsb.ws_set_kernel(hd, wsb.WS_KERNEL_AUTO, 64, 40, 0)
     assert e.value.code == wsb.WS_ERR_BADARG
 
 
