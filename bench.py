@@ -58,6 +58,8 @@ def parse_args():
                          "times; batched = the 64-shot batch for --steps steps")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the 64-shot batched-launch report")
+    ap.add_argument("--shots", type=int, default=64,
+                    help="--case batched: the first N shots of the 64-shot workload")
     ap.add_argument("--no-adjoint", action="store_true",
                     help="skip the 256^3 16-shot adjoint-gradient report")
     ap.add_argument("--no-storage16", action="store_true",
@@ -608,7 +610,7 @@ def run_case(args):
         torch.cuda.synchronize()
         cells = 2 * w.nx * w.ny * w.nz * w.nt   # two gradients timed, one forward-run of cells each
     else:
-        shots = synthetic.batched_shots(nt=K)
+        shots = synthetic.batched_shots(nt=K)[:args.shots]
         hs = [_shot_handle(wsb, x, K + 60) for x in shots]
         b = wsb.ws_batch_create(hs)
         wsb.ws_batch_step(b, 60)

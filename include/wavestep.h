@@ -294,7 +294,12 @@ int ws_set_kernel(ws_t ws, int kernel, int tile_x, int tile_y, int zblock);
  * resident CTAs) on
  * steps written to a scratch field, so the state is unchanged; then select
  * WS_KERNEL_STREAM with the fastest (WS_KERNEL_DIRECT if no tile fits).
- * Results are cached per grid size for the process. Outputs may be NULL.
+ * Results are cached by (GPU name, storage, nx, ny, nz) in the process and
+ * in a text file, so later processes on the same GPU model skip the timing:
+ * the file is $WS_TUNE_CACHE if set, else $XDG_CACHE_HOME/wavestep/tune.txt,
+ * else $HOME/.cache/wavestep/tune.txt (one "gpu|storage|nx|ny|nz|tx|ty|zb"
+ * line per entry; unreadable lines are ignored, an unwritable file leaves
+ * the in-process cache only). Outputs may be NULL.
  * Needs a velocity model and FP32 storage, else STATE. Synchronizes. */
 int ws_autotune(ws_t ws, int *tile_x, int *tile_y, int *zblock);
 

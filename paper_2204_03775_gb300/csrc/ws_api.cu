@@ -61,17 +61,24 @@ size_t field_bytes(const ws::Geom &g) {
     return size_t(g.pnx) * size_t(g.pny) * size_t(g.pnz) * sizeof(float);
 }
 
+// A tensor map of a padded field over its interior only: origin at interior
+// cell (0, 0, 0) (a 128-byte aligned address), extent nx x ny x nz, the
+// padded pitches. The kernels' boxes that reach past the interior (the 4-cell
+// halo of the edge tiles, the ragged end of the last tiles) are filled with
+// zeros by the copy engine without reading memory: exactly the zero halo,
+// and no DRAM traffic for halo or row padding.
 int encode_map(CUtensorMap *map, void *base, const ws::Geom &g, int bx, int by,
                int elem_bytes) {
     PFN_cuTensorMapEncodeTiled_v12000 enc = get_encode_fn();
     if (!enc) return fail(WS_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
-    cuuint64_t dims[3] = {(cuuint64_t)g.pnx, (cuuint64_t)g.pny, (cuuint64_t)g.pnz};
+    cuuint64_t dims[3] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz};
     cuuint64_t strides[2] = {(cuuint64_t)g.pnx * elem_bytes, (cuuint64_t)g.plane * elem_bytes};
     cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 1};
     cuuint32_t estr[3] = {1, 1, 1};
     const CUtensorMapDataType dt =
         elem_bytes == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_UINT16;
-    CUresult r = enc(map, dt, 3, base, dims, strides, box, estr,
+    void *origin = static_cast<char *>(base) + ws::pidx(g, 0, 0, 0) * elem_bytes;
+    CUresult r = enc(map, dt, 3, origin, dims, strides, box, estr,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(WS_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);

@@ -1,6 +1,12 @@
 // Host side of the tiling autotuner (ws_autotune) and of batched shots
 // (ws_batch_*): one launch per step over every shot's items, runs of steps
 // replayed as CUDA graphs, the tile and z-block rule tuned online.
+#include <sys/stat.h>
+#include <unistd.h>
+
+#include <cstdlib>
+#include <string>
+
 #include "ws_host.h"
 
 using namespace wsh;
@@ -57,8 +63,80 @@ std::vector<int> zblock_candidates(int nz, long long tiles, int slots) {
     return z;
 }
 
+// Tilings chosen by ws_autotune, keyed by (GPU name, storage, nx, ny, nz):
+// kept in memory and in a text file (one "gpu|storage|nx|ny|nz|tx|ty|zb"
+// line per entry) at $WS_TUNE_CACHE, else $XDG_CACHE_HOME/wavestep/tune.txt,
+// else $HOME/.cache/wavestep/tune.txt, so a later process on the same GPU
+// model reuses them. Lines that do not parse are ignored; a file that cannot
+// be written leaves the in-memory cache only.
+using TuneKey = std::tuple<std::string, int, int, int, int>;
 std::mutex g_tune_mutex;
-std::map<std::tuple<int, int, int>, ws::StreamTiling> g_tune_cache;
+std::map<TuneKey, ws::StreamTiling> g_tune_cache;
+bool g_tune_loaded = false;
+
+std::string tune_cache_path() {
+    if (const char *p = std::getenv("WS_TUNE_CACHE")) return p;
+    if (const char *x = std::getenv("XDG_CACHE_HOME")) return std::string(x) + "/wavestep/tune.txt";
+    if (const char *h = std::getenv("HOME")) return std::string(h) + "/.cache/wavestep/tune.txt";
+    return std::string();
+}
+
+// Call with g_tune_mutex held.
+void tune_cache_load() {
+    if (g_tune_loaded) return;
+    g_tune_loaded = true;
+    const std::string path = tune_cache_path();
+    if (path.empty()) return;
+    FILE *f = std::fopen(path.c_str(), "r");
+    if (!f) return;
+    char line[512];
+    while (std::fgets(line, sizeof line, f)) {
+        char *bar = std::strchr(line, '|');
+        if (!bar) continue;
+        int st, nx, ny, nz, tx, ty, zb;
+        if (std::sscanf(bar + 1, "%d|%d|%d|%d|%d|%d|%d", &st, &nx, &ny, &nz, &tx, &ty, &zb) != 7)
+            continue;
+        if (!ws::stream_tiling_supported(tx, ty) || zb < 1) continue;
+        g_tune_cache[TuneKey(std::string(line, bar - line), st, nx, ny, nz)] =
+            ws::StreamTiling{tx, ty, zb};
+    }
+    std::fclose(f);
+}
+
+// Rewrite the file with every entry (a temporary file renamed over it).
+// Call with g_tune_mutex held.
+void tune_cache_save() {
+    const std::string path = tune_cache_path();
+    if (path.empty()) return;
+    const size_t slash = path.rfind('/');
+    if (slash != std::string::npos && slash > 0) {
+        const std::string dir = path.substr(0, slash);
+        const size_t s2 = dir.rfind('/');
+        if (s2 != std::string::npos && s2 > 0) mkdir(dir.substr(0, s2).c_str(), 0755);
+        mkdir(dir.c_str(), 0755);
+    }
+    const std::string tmp = path + ".tmp" + std::to_string((long long)getpid());
+    FILE *f = std::fopen(tmp.c_str(), "w");
+    if (!f) return;
+    for (const auto &kv : g_tune_cache)
+        std::fprintf(f, "%s|%d|%d|%d|%d|%d|%d|%d\n", std::get<0>(kv.first).c_str(),
+                     std::get<1>(kv.first), std::get<2>(kv.first), std::get<3>(kv.first),
+                     std::get<4>(kv.first), kv.second.tx, kv.second.ty, kv.second.zb);
+    const bool ok = std::fclose(f) == 0;
+    if (!ok || std::rename(tmp.c_str(), path.c_str()) != 0) std::remove(tmp.c_str());
+}
+
+// The name of the current device ("" if it cannot be read), '|' replaced.
+std::string device_name() {
+    int dev = 0;
+    cudaDeviceProp prop;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess)
+        return std::string();
+    std::string n(prop.name);
+    for (char &c : n)
+        if (c == '|' || c == '\n') c = '_';
+    return n;
+}
 
 }  // namespace
 
@@ -71,9 +149,11 @@ int ws_autotune(ws_t ws, int *tile_x, int *tile_y, int *zblock) {
         return fail(WS_ERR_STATE, "ws_autotune: tunes the FP32 streaming kernel only");
     const ws::Geom &g = ws->g;
     ws::StreamTiling best{0, 0, 0};
+    const TuneKey key(device_name(), ws->storage, g.nx, g.ny, g.nz);
     {
         std::lock_guard<std::mutex> lock(g_tune_mutex);
-        auto it = g_tune_cache.find(std::make_tuple(g.nx, g.ny, g.nz));
+        tune_cache_load();
+        auto it = g_tune_cache.find(key);
         if (it != g_tune_cache.end()) best = it->second;
     }
     if (best.tx == 0) {
@@ -130,7 +210,8 @@ int ws_autotune(ws_t ws, int *tile_x, int *tile_y, int *zblock) {
         }
         if (best.tx != 0) {
             std::lock_guard<std::mutex> lock(g_tune_mutex);
-            g_tune_cache[std::make_tuple(g.nx, g.ny, g.nz)] = best;
+            g_tune_cache[key] = best;
+            tune_cache_save();
         }
     }
     if (best.tx == 0) {   // no tile fits: the direct kernel

@@ -138,7 +138,8 @@ struct AdjointCache {
 namespace wsh {
 
 size_t field_bytes(const ws::Geom &g);
-// A tensor map of a padded field with a (bx, by, 1) box.
+// A tensor map of a padded field over its interior (cells outside read as
+// zeros) with a (bx, by, 1) box.
 int encode_map(CUtensorMap *map, void *base, const ws::Geom &g, int bx, int by,
                int elem_bytes = 4);
 // The handle's maps for its current tiling.

@@ -199,16 +199,18 @@ struct Kern {
 
     // Copy relative plane pr of the item (interior plane z0 - 4 + pr, with
     // its halo) into the g-th ring-A slot use, once its previous plane is
-    // released. The box corner is interior (i0 - 4, j0 - 4), padded
-    // (i0 + kXOff - 4, j0, z0 + pr); x is a multiple of 4 elements.
+    // released. The maps cover the interior only (origin at interior cell 0):
+    // the box corner is (i0 - 4, j0 - 4, z0 - 4 + pr), and whatever of the
+    // box lies outside the grid arrives as zeros without a memory read (the
+    // zero halo). x is a multiple of 4 elements (16 bytes).
     static __device__ __forceinline__ bool produce_a(R &rg, float *ringA, const Job &jb, unsigned g,
                                                      int pr, unsigned *status) {
         const int slot = g & (NA - 1);
         if (!wait_phase(&rg.emptyA[slot], ((g / NA) & 1u) ^ 1u, &rg.abort, status)) return false;
         rg.issuedA[slot]++;
         mbar_arrive_expect_tx(&rg.fullA[slot], Cfg::kSlotABytes);
-        tma_load_3d(ringA + slot * Cfg::kSlotA, jb.u, &rg.fullA[slot], jb.it.i0 + kXOff - kHalo,
-                    jb.it.j0, jb.it.z0 + pr);
+        tma_load_3d(ringA + slot * Cfg::kSlotA, jb.u, &rg.fullA[slot], jb.it.i0 - kHalo,
+                    jb.it.j0 - kHalo, jb.it.z0 - kHalo + pr);
         return true;
     }
 
@@ -220,10 +222,8 @@ struct Kern {
         rg.issuedB[slot]++;
         float *dst = ringB + slot * (2 * Cfg::kTile);
         mbar_arrive_expect_tx(&rg.fullB[slot], Cfg::kSlotBBytes);
-        tma_load_3d(dst, jb.up, &rg.fullB[slot], jb.it.i0 + kXOff, jb.it.j0 + kHalo,
-                    jb.it.z0 + b + kHalo);
-        tma_load_3d(dst + Cfg::kTile, jb.w, &rg.fullB[slot], jb.it.i0 + kXOff, jb.it.j0 + kHalo,
-                    jb.it.z0 + b + kHalo);
+        tma_load_3d(dst, jb.up, &rg.fullB[slot], jb.it.i0, jb.it.j0, jb.it.z0 + b);
+        tma_load_3d(dst + Cfg::kTile, jb.w, &rg.fullB[slot], jb.it.i0, jb.it.j0, jb.it.z0 + b);
         return true;
     }
 

@@ -401,14 +401,15 @@ struct Kern16 {
     };
 
     // U of relative plane pr (interior plane z0 - 4 + pr, with its halo) into
-    // ring-A slot `slot`. Box corner: interior (i0 - 8, j0 - 4), padded
-    // (i0 + kXOff - 8, j0, z0 + pr); x is a multiple of 8 elements (16 bytes).
+    // ring-A slot `slot`. The maps cover the interior only: box corner
+    // (i0 - 8, j0 - 4, z0 - 4 + pr), cells outside the grid arrive as zeros
+    // without a memory read; x is a multiple of 8 elements (16 bytes).
     static __device__ __forceinline__ void issue_a(B &br, uint16_t *ringA, const Maps16 &mp,
                                                    const Item &it, int slot, int pr) {
         br.issuedA[slot]++;
         mbar_arrive_expect_tx(&br.fullA[slot], Cfg::kSlotABytes);
-        tma_load_3d(ringA + slot * Cfg::kSlotA, &mp.u, &br.fullA[slot], it.i0 + kXOff - Cfg::kLead,
-                    it.j0, it.z0 + pr);
+        tma_load_3d(ringA + slot * Cfg::kSlotA, &mp.u, &br.fullA[slot], it.i0 - Cfg::kLead,
+                    it.j0 - kHalo, it.z0 - kHalo + pr);
     }
 
     // D and W of interior plane z0 + b into ring-B slot `slot`.
@@ -417,9 +418,8 @@ struct Kern16 {
         br.issuedB[slot]++;
         uint16_t *dst = ringB + slot * Cfg::kSlotB;
         mbar_arrive_expect_tx(&br.fullB[slot], Cfg::kSlotBBytes);
-        tma_load_3d(dst, &mp.d, &br.fullB[slot], it.i0 + kXOff, it.j0 + kHalo, it.z0 + b + kHalo);
-        tma_load_3d(dst + Cfg::kTile, &mp.w, &br.fullB[slot], it.i0 + kXOff, it.j0 + kHalo,
-                    it.z0 + b + kHalo);
+        tma_load_3d(dst, &mp.d, &br.fullB[slot], it.i0, it.j0, it.z0 + b);
+        tma_load_3d(dst + Cfg::kTile, &mp.w, &br.fullB[slot], it.i0, it.j0, it.z0 + b);
     }
 
     // The stencil sum of one row's 4 cells (two FP32x2 pairs): c0 u +

@@ -131,6 +131,40 @@ def test_autotune_keeps_state_and_results():
     assert wsb.ws_autotune(_handle(s)) == (tx, ty, zb)
 
 
+def test_autotune_cache_persists_across_processes(tmp_path):
+    """The tuned tiling is written to the cache file ($WS_TUNE_CACHE) keyed by
+    GPU name, storage and grid size; a new process tuning the same grid finds
+    it there and times nothing (no kernel launches)."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    path = tmp_path / "tune.txt"
+    code = (
+        "import sys; sys.path.insert(0, %r)\n"
+        "import numpy as np\n"
+        "import paper_2204_03775_gb300 as wsb\n"
+        "wsb.load_library(build_if_missing=True)\n"
+        "h = wsb.ws_create(130, 40, 30, 10.0, 1e-3)\n"
+        "wsb.ws_set_velocity(h, np.full((30, 40, 130), 2000.0, np.float32))\n"
+        "n0 = wsb.ws_launch_count(h)\n"
+        "t = wsb.ws_autotune(h)\n"
+        "print(*t, wsb.ws_launch_count(h) - n0)\n" % root)
+    env = dict(os.environ, WS_TUNE_CACHE=str(path))
+    runs = [subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                           timeout=300) for _ in range(2)]
+    for r in runs:
+        assert r.returncode == 0, r.stderr
+    first, second = (list(map(int, r.stdout.split())) for r in runs)
+    assert first[3] > 0 and second[3] == 0, (first, second)
+    assert first[:3] == second[:3]
+    lines = path.read_text().splitlines()
+    assert len(lines) == 1
+    gpu, storage, nx, ny, nz, tx, ty, zb = lines[0].split("|")
+    assert gpu and (int(storage), int(nx), int(ny), int(nz)) == (wsb.WS_STORAGE_FP32, 130, 40, 30)
+    assert [int(tx), int(ty), int(zb)] == first[:3]
+
+
 def test_batch_errors():
     s = _shot((72, 40, 30), 1, 10)
     h = _handle(s)
