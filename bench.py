@@ -32,7 +32,7 @@ METRIC = "Gpoint-updates/s & % of HBM roofline, 25-pt wave step, FP32 vs BF16 at
 UNIT = "Gpoint-updates/s"
 BYTES_PER_POINT = 16  # read u^n, u^{n-1}, (V dt/h)^2; write u^{n+1} (FP32)
 FALLBACK_HBM_GBS = 6800.0
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "step_stream_layered1024_ncu.txt")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "step_stream_layered512_traffic.txt")
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_2204_03775_gb300", "csrc", f)
                   for f in ("ws_kernels_stream.cu", "ws_ptx.cuh", "ws_internal.h")]
 
@@ -77,20 +77,21 @@ def kernel_sources_digest() -> str:
     return h.hexdigest()
 
 
-def recorded_traffic():
-    """DRAM bytes per launch from the committed ncu summary, if it matches the kernel source."""
+def recorded_traffic(cells):
+    """DRAM bytes per launch of the streaming kernel over `cells` cells: the
+    committed ncu summary's bytes per cell (a small-case capture) times the
+    cells, if the summary matches the current kernel sources; else None."""
     try:
         fields = {}
         with open(TRAFFIC_FILE) as f:
             for line in f:
-                if ":" in line:
-                    k, v = line.split(":", 1)
-                    fields[k.strip()] = v.strip()
+                if line.startswith("#") or ":" not in line:
+                    continue
+                k, v = line.split(":", 1)
+                fields[k.strip()] = v.strip()
         if fields.get("kernel_sources_sha256") != kernel_sources_digest():
             return None
-        if fields.get("workload_cells") != str(1024 ** 3):
-            return None
-        return float(fields["traffic_bytes_per_launch"])
+        return float(fields["bytes_per_cell"]) * cells
     except (OSError, KeyError, ValueError):
         return None
 
@@ -773,7 +774,9 @@ def main():
                    "zblock": args.zblock, "l2": "inputs larger than L2 (3 x 4.4 GB per step)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": recorded_traffic(),
+                     "frac": achieved / peak, "traffic": recorded_traffic(npts),
+                     "traffic_source": "profiles/step_stream_layered512_traffic.txt: DRAM bytes "
+                                       "per cell of a 512^3 capture x the launch's cells",
                      "peak_source": peak_kind,
                      "bytes_per_point": BYTES_PER_POINT,
                      "kernel_ms": 1e3 * avg_launch},

@@ -271,21 +271,28 @@ int ws_forward(ws_t ws);
  * device from max|u^n| and the source amplitude so that the field's maximum
  * sits near 2^12 (16x under the FP16 limit); FP16 then holds values down to
  * ~2^-36 of that maximum and smaller ones as zero. The current state is converted
- * (rounded once). 16-bit storage runs its own streaming kernel with a 64x16
- * tile and needs nx >= 64, ny >= 16, else BADARG. ws_read_field, ws_write_field
- * and ws_energy convert to and from FP32 (ws_energy then uses the FP32
- * model). Relative L2 error against the FP64 oracle, measured on the layered
- * survey at 256^3 after 100, 500, 1000 steps: FP16 8.6e-4, 2.8e-3, 5.4e-3;
- * BF16 6.6e-3, 2.3e-2, 4.4e-2 (FP32 storage 5.7e-7 ... 2.5e-6); at 1024^3
- * after 100 steps FP16 7.9e-4, BF16 6.2e-3. This realizes the reduced-precision storage
- * that the paper contrasts with its FP32-only arithmetic (Section I). */
+ * (rounded once). 16-bit storage runs its own streaming kernel with a 64 x ty
+ * tile (ty = 24 by default, 16 on grids with ny < 24; 16, 24 or 48 through
+ * ws_set_kernel), single grids only (batches and the adjoint gradient need
+ * FP32 storage), and needs nx >= 64, ny >= 16, else BADARG. ws_read_field,
+ * ws_write_field and ws_energy convert to and from FP32 (ws_energy then uses
+ * the FP32 model). Relative L2 error against the FP64 oracle, measured on the
+ * layered survey at 512^3 after 100, 500, 1000 steps: FP16 8.5e-4, 2.8e-3,
+ * 4.1e-3; BF16 6.1e-3, 2.3e-2, 3.5e-2 (FP32 storage 5.3e-7 ... 1.9e-6): FP16
+ * stays within 1e-2, BF16 only for about the first 100 steps (its 8-bit
+ * significand's rounding errors add up like a random walk); at 1024^3 after
+ * 100 steps FP16 7.6e-4, BF16 5.9e-3. Speed on the 1024^3 survey: 1.12x (FP16)
+ * and 1.13x (BF16) of FP32 storage. This realizes the reduced-precision
+ * storage that the paper contrasts with its FP32-only arithmetic (Section I). */
 int ws_set_storage(ws_t ws, int storage);
 
 /* Choose the step kernel (WS_KERNEL_*) and, for WS_KERNEL_STREAM, its tile:
- * tile_x x tile_y in {32x8, 32x16, 64x8, 64x16, 64x32} (0, 0 = keep the
- * current tile; the default is 64x8), zblock >= 1 planes per work item
- * (0 = default: about 200 planes, fewer on small grids). WS_KERNEL_STREAM needs nx >= tile_x and ny >= tile_y;
- * else BADARG. */
+ * tile_x x tile_y in {32x8, 32x16, 64x8, 64x16, 64x32} for the FP32 kernel
+ * (0, 0 = keep the current tile; the default is 64x8) or in {64x16, 64x24,
+ * 64x48} for the 16-bit kernel (64x16 selects both; a 16-bit tile leaves the
+ * FP32 tile unchanged and needs nx >= 64 and ny >= tile_y), zblock >= 1 planes
+ * per work item (0 = default: about 200 planes, fewer on small grids).
+ * WS_KERNEL_STREAM needs nx >= tile_x and ny >= tile_y; else BADARG. */
 int ws_set_kernel(ws_t ws, int kernel, int tile_x, int tile_y, int zblock);
 
 /* Pick the streaming kernel's tile and z-block for this handle's grid by
