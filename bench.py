@@ -614,6 +614,9 @@ def run_case(args):
         shots = synthetic.batched_shots(nt=K)[:args.shots]
         hs = [_shot_handle(wsb, x, K + 60) for x in shots]
         b = wsb.ws_batch_create(hs)
+        tx, ty = (int(x) for x in args.tile.split("x"))
+        if tx:   # a fixed tiling (--zblock is then the z-block rule, see ws_batch_set_tiling)
+            wsb.ws_batch_set_tiling(b, tx, ty, args.zblock)
         wsb.ws_batch_step(b, 60)
         wsb.ws_batch_synchronize(b)
         t0 = time.perf_counter()
