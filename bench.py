@@ -412,7 +412,7 @@ def batched_report(peak):
             wsb.ws_set_receivers(h, w.receivers, nt)
 
     t0 = time.perf_counter()
-    wsb.ws_batch_step(b, 60)            # online tuning: 25 candidates x 2 steps, then the best
+    wsb.ws_batch_step(b, 60)            # online tuning: 18 candidates x 2 steps, then the best
     wsb.ws_batch_synchronize(b)
     tune_s = time.perf_counter() - t0
     tiling = wsb.ws_batch_get_tiling(b)

@@ -291,12 +291,15 @@ int ws_set_storage(ws_t ws, int storage);
  * (0, 0 = keep the current tile; the default is 64x8) or in {64x16, 64x24,
  * 64x48} for the 16-bit kernel (64x16 selects both; a 16-bit tile leaves the
  * FP32 tile unchanged and needs nx >= 64 and ny >= tile_y), zblock >= 1 planes
- * per work item (0 = default: about 200 planes, fewer on small grids).
+ * per work item (0 = default: blocks of about 200 planes with a last block
+ * about a quarter as long, so that the last items of a launch are short;
+ * fewer planes on small grids).
  * WS_KERNEL_STREAM needs nx >= tile_x and ny >= tile_y; else BADARG. */
 int ws_set_kernel(ws_t ws, int kernel, int tile_x, int tile_y, int zblock);
 
 /* Pick the streaming kernel's tile and z-block for this handle's grid by
- * timing the candidates (every tile that fits; z-blocks giving the default
+ * timing the candidates (every tile of 64x8, 32x8, 32x16 that fits: 64x16
+ * and 64x32 hold too few registers per thread and are never faster; z-blocks giving the default
  * length and item counts just below and just above 1 .. 8 waves of the
  * resident CTAs) on
  * steps written to a scratch field, so the state is unchanged; then select

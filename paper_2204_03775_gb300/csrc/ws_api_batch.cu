@@ -41,8 +41,11 @@ struct ws_batch {
 
 namespace {
 
-// Tiles of the streaming kernel, in the order the tuners try them.
-constexpr int kTileCands[5][2] = {{64, 8}, {32, 8}, {32, 16}, {64, 16}, {64, 32}};
+// Tiles of the streaming kernel, in the order the tuners try them. 64 x 16
+// and 64 x 32 are left out: with 9 and 17 warps per CTA one SM sub-partition
+// holds 5 of their warps, which caps them at 96 registers per thread, and
+// they spill (measured at less than half the speed of these three).
+constexpr int kTileCands[3][2] = {{64, 8}, {32, 8}, {32, 16}};
 
 // z-block candidates for a grid of nz planes cut into `tiles` xy tiles: the
 // default, and for m = 1 .. 8 the z blocks whose item count comes closest to

@@ -89,19 +89,27 @@ struct Job {
     bool stall;
 };
 
-// What the consumers need of an item's grid.
+// What the consumers need of an item's grid: fields read at the start of an
+// item or on every plane, and accessors for what only source injection and
+// receiver recording use.
 struct View {
     Geom g;
     const float *gx, *gy, *gz;
-    const SourceSample *src;   // this step's source samples
-    int nsrc;
-    float *traces;             // [nrec][nt_max]
-    int nt_max;
-    long long trace_step;
     float *out;                // u^{n+1} field (padded)
     long long lap_delta;       // L u^n goes to out + lap_delta (0: not stored)
     const int *rec_ptr;        // per-tile receiver ranges, or null
-    const RecEntry *rec;
+    const RecEntry *rec_;
+    const SourceSample *src_;  // this step's source samples
+    int nsrc_;
+    float *traces_;            // [nrec][nt_max]
+    int nt_max_;
+    long long trace_step_;
+    __device__ __forceinline__ const SourceSample *src() const { return src_; }
+    __device__ __forceinline__ int nsrc() const { return nsrc_; }
+    __device__ __forceinline__ const RecEntry *rec() const { return rec_; }
+    __device__ __forceinline__ float *traces() const { return traces_; }
+    __device__ __forceinline__ int nt_max() const { return nt_max_; }
+    __device__ __forceinline__ long long trace_step() const { return trace_step_; }
 };
 
 // Items of one grid; everything comes from kernel parameters. kLap: the
@@ -109,6 +117,7 @@ struct View {
 template <int TX, int TY, bool kLap>
 struct OneGrid {
     static constexpr bool kStoreLap = kLap;
+    using V = View;
     const StreamMaps &mp;
     const StepArgs &a;
     float *up;
@@ -126,17 +135,38 @@ struct OneGrid {
         v->gx = a.gx;
         v->gy = a.gy;
         v->gz = a.gz;
-        v->src = a.src.s;
-        v->nsrc = a.src.n;
-        v->traces = a.traces;
-        v->nt_max = a.nt_max;
-        v->trace_step = a.trace_step;
+        v->src_ = a.src.s;
+        v->nsrc_ = a.src.n;
+        v->traces_ = a.traces;
+        v->nt_max_ = a.nt_max;
+        v->trace_step_ = a.trace_step;
         v->out = up;
         v->lap_delta = kLap ? a.lap - up : 0;
         v->rec_ptr = rec_ptr;
-        v->rec = rec;
+        v->rec_ = rec;
         return item_of(item, tiles_x, ntiles, zb, a.g.nz, TX, TY);
     }
+};
+
+// The view of a batch item: the fields of every plane in registers, the rest
+// read from the shot's descriptor where they are used (held in registers for
+// the whole item they would not fit the batched kernel's register budget).
+struct BatchView {
+    Geom g;
+    const float *gx, *gy, *gz;
+    float *out;
+    static constexpr long long lap_delta = 0;
+    const int *rec_ptr;
+    const BatchShot *shot;
+    int t;
+    __device__ __forceinline__ const SourceSample *src() const {
+        return shot->src + (long long)t * shot->nsrc;
+    }
+    __device__ __forceinline__ int nsrc() const { return shot->nsrc; }
+    __device__ __forceinline__ const RecEntry *rec() const { return shot->rec; }
+    __device__ __forceinline__ float *traces() const { return shot->traces; }
+    __device__ __forceinline__ int nt_max() const { return shot->nt_max; }
+    __device__ __forceinline__ long long trace_step() const { return shot->trace_col0 + t; }
 };
 
 // Items of a batch of shots: items[q] = (shot, item of that shot), step t of
@@ -144,6 +174,7 @@ struct OneGrid {
 template <int TX, int TY>
 struct ShotBatch {
     static constexpr bool kStoreLap = false;
+    using V = BatchView;
     const BatchShot *shots;
     const int2 *items;
     int n, t;
@@ -156,7 +187,7 @@ struct ShotBatch {
         return Job{item_of(e.y, s.tiles_x, s.ntiles, s.zb, s.g.nz, TX, TY), &s.halo[p],
                    &s.tile[1 - p], &s.w, t == 0 && e.y == s.stall_item};
     }
-    __device__ __forceinline__ Item view(int item, View *v) const {
+    __device__ __forceinline__ Item view(int item, BatchView *v) const {
         const int2 e = items[item];
         const BatchShot &s = shots[e.x];
         const int p = s.cur0 ^ (t & 1);
@@ -164,15 +195,10 @@ struct ShotBatch {
         v->gx = s.gx;
         v->gy = s.gy;
         v->gz = s.gz;
-        v->nsrc = s.nsrc;
-        v->src = s.src + (long long)t * s.nsrc;
-        v->traces = s.traces;
-        v->nt_max = s.nt_max;
-        v->trace_step = s.trace_col0 + t;
         v->out = s.buf[1 - p];
-        v->lap_delta = 0;
         v->rec_ptr = s.rec_ptr;
-        v->rec = s.rec;
+        v->shot = &s;
+        v->t = t;
         return item_of(e.y, s.tiles_x, s.ntiles, s.zb, s.g.nz, TX, TY);
     }
 };
@@ -263,9 +289,9 @@ struct Kern {
 
     // Plane k of the item, with the rotation R = (k - z0) mod 9 fixed at
     // compile time.
-    template <int RQ, bool kLap>
+    template <int RQ, bool kLap, class VT>
     static __device__ __forceinline__ void plane_step(Walk &wk, R &rg, const float *ringA,
-                                                      const float *ringB, const View &v,
+                                                      const float *ringB, const VT &v,
                                                       const Coeffs &c, unsigned *status,
                                                       const Item &it, int k, int i, int j,
                                                       int offA, int offB) {
@@ -344,8 +370,9 @@ struct Kern {
         }
         float4 out = make_float4(o[0].x, o[0].y, o[1].x, o[1].y);
         if (wk.src_mask) {
-            for (int qs = 0; qs < v.nsrc; ++qs) {
-                const SourceSample ss = v.src[qs];
+            const SourceSample *srcs = v.src();
+            for (int qs = 0, ns = v.nsrc(); qs < ns; ++qs) {
+                const SourceSample ss = srcs[qs];
                 if (((wk.src_mask >> qs) & 1u) && ss.k == k && ss.j == j) {
 #pragma unroll
                     for (int l = 0; l < 4; ++l)
@@ -373,8 +400,8 @@ struct Kern {
         }
         wk.out_k += v.g.plane;
         if (k == wk.rnext_k)
-            record_plane(out, 1.0f, k, &wk.rcur, wk.rend, &wk.rnext_k, v.rec, v.traces, v.nt_max,
-                         v.trace_step);
+            record_plane(out, 1.0f, k, &wk.rcur, wk.rend, &wk.rnext_k, v.rec(), v.traces(),
+                         v.nt_max(), v.trace_step());
 #undef QI
 #undef BI
     }
@@ -402,7 +429,7 @@ struct Kern {
         wk.gAw = wk.gAr = wk.gB = 0;
         wk.ok = true;
         for (int item = blockIdx.x; item < src.nitems() && wk.ok; item += gridDim.x) {
-            View v;
+            typename S::V v;
             const Item it = src.view(item, &v);
             const Geom &g = v.g;
             const int i = it.i0 + 4 * tx;
@@ -418,8 +445,9 @@ struct Kern {
                 if (wk.nvalid > 3) wk.gxy.w = v.gx[i + 3] * gyj;
             }
             wk.src_mask = 0u;
-            for (int qs = 0; qs < v.nsrc; ++qs) {
-                const SourceSample ss = v.src[qs];
+            const SourceSample *srcs = v.src();
+            for (int qs = 0, ns = v.nsrc(); qs < ns; ++qs) {
+                const SourceSample ss = srcs[qs];
                 if (ss.i >= it.i0 && ss.i < it.i0 + TX && ss.j >= it.j0 && ss.j < it.j0 + TY &&
                     ss.k >= it.z0 && ss.k < it.z1)
                     wk.src_mask |= 1u << qs;
@@ -428,9 +456,9 @@ struct Kern {
             if (v.rec_ptr != nullptr) {
                 const int r = it.tile * (Cfg::kConsumers / 32) + (tid >> 5);
                 wk.rend = v.rec_ptr[r + 1];
-                wk.rcur = first_entry(v.rec, v.rec_ptr[r], wk.rend, it.z0);
+                wk.rcur = first_entry(v.rec(), v.rec_ptr[r], wk.rend, it.z0);
             }
-            wk.rnext_k = wk.rcur < wk.rend ? v.rec[wk.rcur].k : INT_MAX;
+            wk.rnext_k = wk.rcur < wk.rend ? v.rec()[wk.rcur].k : INT_MAX;
             wk.out_k = v.out + pidx(g, col_ok ? i : 0, col_ok ? j : 0, it.z0);
 #pragma unroll
             for (int d = 0; d < 2; ++d)

@@ -388,10 +388,19 @@ __device__ __forceinline__ void store16(uint16_t *p, const uint2 st) {
     asm volatile("st.global.cs.v2.u32 [%0], {%1, %2};" ::"l"(p), "r"(st.x), "r"(st.y) : "memory");
 }
 
+// Planes per loop trip: 9 (the ring depth: every ring slot and queue index
+// is a compile-time constant) or 3 (a third of the code, with the queue
+// renamed by moves after each trip and the ring-A slots computed).
+#ifndef WS16_TRIP
+#define WS16_TRIP 3
+#endif
+
 template <class Fmt, int TX, int TY, int NA, int NB>
 struct Kern16 {
     using Cfg = Cfg16<TX, TY, NA, NB>;
     using B = Bars16<NA, NB>;
+    static constexpr int NU = WS16_TRIP;
+    static_assert(NU == 9 || NU == 3, "9 or 3 planes per trip");
 
     // factors of one launch (uniform)
     struct Factors {
@@ -489,7 +498,7 @@ struct Kern16 {
         return make_float4(o[0].x, o[0].y, o[1].x, o[1].y);
     }
 
-    // Plane k of the walk, RQ = (k - z0) mod 9; tp: parity of the trip;
+    // Plane k of the walk, RQ = (k - z0) mod NU; tp: parity of the trip;
     // so: byte offset of plane k's staging buffer; pk: U' of (i, j, k).
     template <int RQ>
     static __device__ __forceinline__ void plane_step(Walk16 &wk, const Ctx16 &cx, B &br,
@@ -499,23 +508,36 @@ struct Kern16 {
                                                       unsigned so, uint16_t *pk, int k,
                                                       unsigned tp, const RecEntry *rec) {
         constexpr int Q8 = (RQ + 8) % 9, Q4 = (RQ + 4) % 9;
-        constexpr int SA_OWN = (RQ + 8) % NA, SA_HALO = (RQ + 4) % NA, SB = RQ % NB;
-        // fill parities: relative plane r + 8 fills slot SA_OWN for the
-        // (trip + (RQ + 8) / 9)-th time; plane r fills SB for the (3 trip + RQ / 3)-th
-        constexpr unsigned PA = ((RQ + 8) / NA) & 1u, PB = (RQ / NB) & 1u;
-        constexpr int OA_OWN = SA_OWN * Cfg::kSlotABytes, OA_HALO = SA_HALO * Cfg::kSlotABytes;
+        constexpr int SB = RQ % NB;
+        // plane r fills ring-B slot SB for the (NU trip / 3 + RQ / 3)-th time
+        constexpr unsigned PB = (RQ / NB) & 1u;
         constexpr int OB = SB * Cfg::kSlotBBytes;
         constexpr int RA = Cfg::kRowW * 2, RB = TX * 2, WB = Cfg::kTile * 2, RS = Cfg::kSW * 4;
         const int r = k - cx.z0;
+        // ring-A slots of relative planes r + 8 (own cells) and r + 4 (halo),
+        // and the parity of the fill the first is waited for
+        int sa_own, sa_halo;
+        unsigned pa;
+        if constexpr (NU == 9) {
+            sa_own = (RQ + 8) % NA;
+            sa_halo = (RQ + 4) % NA;
+            pa = tp ^ (((RQ + 8) / NA) & 1u);
+        } else {
+            const int x = r - RQ - (r - RQ) / NA * NA;   // (trip start) mod 9
+            sa_own = x + RQ + 8 >= NA ? x + RQ + 8 - NA : x + RQ + 8;
+            sa_halo = x + RQ + 4 >= NA ? x + RQ + 4 - NA : x + RQ + 4;
+            pa = (unsigned)((r + 8) / NA) & 1u;
+        }
+        const unsigned oa_own = sa_own * Cfg::kSlotABytes, oa_halo = sa_halo * Cfg::kSlotABytes;
 
         // U of plane k + 4 (ring A) and D, W of plane k (ring B): one test of
         // both barriers, the bounded waits only when either is not complete
-        if (!(mbar_try_wait(&br.fullA[SA_OWN], tp ^ PA) & mbar_try_wait(&br.fullB[SB], tp ^ PB)))
-            wk.ok = wait_phase(&br.fullA[SA_OWN], tp ^ PA, &br.abort, a.status) &&
+        if (!(mbar_try_wait(&br.fullA[sa_own], pa) & mbar_try_wait(&br.fullB[SB], tp ^ PB)))
+            wk.ok = wait_phase(&br.fullA[sa_own], pa, &br.abort, a.status) &&
                     wait_phase(&br.fullB[SB], tp ^ PB, &br.abort, a.status) && wk.ok;
         // this thread's two rows of plane k + 4 -> the queue (decoded once)
-        wk.q[Q8][0] = Fmt::decode(lds2_at<OA_OWN>(cx.aOwn));
-        wk.q[Q8][1] = Fmt::decode(lds2_at<OA_OWN + RA>(cx.aOwn));
+        wk.q[Q8][0] = Fmt::decode(lds2_at<0>(cx.aOwn + oa_own));
+        wk.q[Q8][1] = Fmt::decode(lds2_at<RA>(cx.aOwn + oa_own));
         // D and W of plane k (raw; decoded where they are used)
         const uint2 dr0 = lds2_at<OB>(cx.bOwn), dr1 = lds2_at<OB + RB>(cx.bOwn);
         const uint2 wr0 = lds2_at<OB + WB>(cx.bOwn), wr1 = lds2_at<OB + WB + RB>(cx.bOwn);
@@ -527,16 +549,16 @@ struct Kern16 {
         sts4_at<0>(st, wk.q[Q4][0]);
         sts4_at<RS>(st, wk.q[Q4][1]);
         if (Cfg::kAllFirst || cx.unit1)
-            sts4_at<0>(cx.sUnit1 + so, Fmt::decode(lds2_at<OA_HALO>(cx.aUnit1)));
+            sts4_at<0>(cx.sUnit1 + so, Fmt::decode(lds2_at<0>(cx.aUnit1 + oa_halo)));
         if (Cfg::kSecond && cx.unit2)
-            sts4_at<0>(cx.sUnit2 + so, Fmt::decode(lds2_at<OA_HALO>(cx.aUnit2)));
+            sts4_at<0>(cx.sUnit2 + so, Fmt::decode(lds2_at<0>(cx.aUnit2 + oa_halo)));
         wk.ok = __syncthreads_and(wk.ok) != 0;
         if (!wk.ok) return;
         // every thread is done with ring-A slot SA_HALO (plane k) and ring-B
         // slot SB: refill them with planes k + 9 (U, from warp 0) and k + 3
         // (D, W, from warp 1)
         if (threadIdx.x == 0 && r + 4 + NA < cx.nplanes)
-            issue_a(br, ringA, mp, it, SA_HALO, r + 4 + NA);
+            issue_a(br, ringA, mp, it, sa_halo, r + 4 + NA);
         if (threadIdx.x == 32 && r + NB < cx.nb) issue_b(br, ringB, mp, it, SB, r + NB);
 
         const float4 xl0 = lds4_at<-16>(st), xr0 = lds4_at<16>(st);
@@ -617,7 +639,25 @@ struct Kern16 {
         wk.amax = Fmt::amax(Fmt::amax(wk.amax, su1.x), su1.y);
     }
 
-    // planes kb + RQ .. kb + NA - 1 of a trip; false once the item ends.
+    // After a trip of 3 planes the queue holds planes k-1 .. k+7 in slots
+    // rotated by 3: rename them (the 9-plane trip needs no renaming).
+    static __device__ __forceinline__ void rotate_queue(Walk16 &wk) {
+        if constexpr (NU % 9 != 0) {
+            float4 t[9][2];
+#pragma unroll
+            for (int m = 0; m < 9; ++m) {
+                t[m][0] = wk.q[(m + NU) % 9][0];
+                t[m][1] = wk.q[(m + NU) % 9][1];
+            }
+#pragma unroll
+            for (int m = 0; m < 9; ++m) {
+                wk.q[m][0] = t[m][0];
+                wk.q[m][1] = t[m][1];
+            }
+        }
+    }
+
+    // planes kb + RQ .. kb + NU - 1 of a trip; false once the item ends.
     // se / so: staging byte offsets of even / odd RQ; pk: U' of (i, j, kb)
     template <int RQ>
     static __device__ __forceinline__ bool planes(Walk16 &wk, const Ctx16 &cx, B &br,
@@ -626,7 +666,7 @@ struct Kern16 {
                                                   const StepArgs &a, const Factors &fc,
                                                   unsigned se, unsigned so, uint16_t *pk, int kb,
                                                   unsigned tp, const RecEntry *rec) {
-        if constexpr (RQ < NA) {
+        if constexpr (RQ < NU) {
             if (kb + RQ >= cx.z1) return false;
             plane_step<RQ>(wk, cx, br, ringA, ringB, mp, it, a, fc, (RQ & 1) ? so : se, pk,
                            kb + RQ, tp, rec);
@@ -788,12 +828,13 @@ __global__ void __launch_bounds__(Cfg16<TX, TY, NA, NB>::kThreads, Cfg16<TX, TY,
             for (int pr = NA; pr < NA + kHalo && pr < nplanes; ++pr)
                 K::issue_a(br, ringA, maps, it, pr - NA, pr);
         unsigned tp = 0;
-        for (int kb = it.z0;; kb += NA, tp ^= 1u) {
+        for (int kb = it.z0;; kb += K::NU, tp ^= 1u) {
             // staging buffer of plane k: k & 1
             const unsigned se = (kb & 1) * Cfg::kStageBytes, sodd = Cfg::kStageBytes - se;
             if (!K::template planes<0>(wk, cx, br, ringA, ringB, maps, it, a, fc, se, sodd,
                                        pu + (long long)(kb - it.z0) * cx.plane, kb, tp, rec))
                 break;
+            K::rotate_queue(wk);
         }
     }
 
