@@ -506,7 +506,8 @@ struct Kern16 {
                                                       const Maps16 &mp, const Item &it,
                                                       const StepArgs &a, const Factors &fc,
                                                       unsigned so, uint16_t *pk, int k,
-                                                      unsigned tp, const RecEntry *rec) {
+                                                      unsigned tp, int ts, unsigned wp,
+                                                      const RecEntry *rec) {
         constexpr int Q8 = (RQ + 8) % 9, Q4 = (RQ + 4) % 9;
         constexpr int SB = RQ % NB;
         // plane r fills ring-B slot SB for the (NU trip / 3 + RQ / 3)-th time
@@ -515,18 +516,20 @@ struct Kern16 {
         constexpr int RA = Cfg::kRowW * 2, RB = TX * 2, WB = Cfg::kTile * 2, RS = Cfg::kSW * 4;
         const int r = k - cx.z0;
         // ring-A slots of relative planes r + 8 (own cells) and r + 4 (halo),
-        // and the parity of the fill the first is waited for
+        // and the parity of the fill the first is waited for: with the trip
+        // starting at relative plane 9 w + ts, plane r + 8 fills its slot for
+        // the (w + [ts + RQ + 8 >= 9])-th time (wp = w & 1)
         int sa_own, sa_halo;
         unsigned pa;
         if constexpr (NU == 9) {
             sa_own = (RQ + 8) % NA;
             sa_halo = (RQ + 4) % NA;
-            pa = tp ^ (((RQ + 8) / NA) & 1u);
+            pa = wp ^ (((RQ + 8) / NA) & 1u);
         } else {
-            const int x = r - RQ - (r - RQ) / NA * NA;   // (trip start) mod 9
-            sa_own = x + RQ + 8 >= NA ? x + RQ + 8 - NA : x + RQ + 8;
-            sa_halo = x + RQ + 4 >= NA ? x + RQ + 4 - NA : x + RQ + 4;
-            pa = (unsigned)((r + 8) / NA) & 1u;
+            const bool wrap = ts + RQ + 8 >= NA;
+            sa_own = wrap ? ts + RQ + 8 - NA : ts + RQ + 8;
+            sa_halo = ts + RQ + 4 >= NA ? ts + RQ + 4 - NA : ts + RQ + 4;
+            pa = wp ^ (unsigned)wrap;
         }
         const unsigned oa_own = sa_own * Cfg::kSlotABytes, oa_halo = sa_halo * Cfg::kSlotABytes;
 
@@ -665,15 +668,16 @@ struct Kern16 {
                                                   const Maps16 &mp, const Item &it,
                                                   const StepArgs &a, const Factors &fc,
                                                   unsigned se, unsigned so, uint16_t *pk, int kb,
-                                                  unsigned tp, const RecEntry *rec) {
+                                                  unsigned tp, int ts, unsigned wp,
+                                                  const RecEntry *rec) {
         if constexpr (RQ < NU) {
             if (kb + RQ >= cx.z1) return false;
             plane_step<RQ>(wk, cx, br, ringA, ringB, mp, it, a, fc, (RQ & 1) ? so : se, pk,
-                           kb + RQ, tp, rec);
+                           kb + RQ, tp, ts, wp, rec);
             // wk.ok is the same in every thread after the plane barrier
             if (!wk.ok) return false;
             return planes<RQ + 1>(wk, cx, br, ringA, ringB, mp, it, a, fc, se, so,
-                                  pk + cx.plane, kb, tp, rec);
+                                  pk + cx.plane, kb, tp, ts, wp, rec);
         }
         return true;
     }
@@ -827,14 +831,23 @@ __global__ void __launch_bounds__(Cfg16<TX, TY, NA, NB>::kThreads, Cfg16<TX, TY,
         if (tid == 0)
             for (int pr = NA; pr < NA + kHalo && pr < nplanes; ++pr)
                 K::issue_a(br, ringA, maps, it, pr - NA, pr);
-        unsigned tp = 0;
+        // tp: trip parity; ts, wp: the trip's first relative plane mod 9 and
+        // the parity of its quotient (the ring-A wrap count)
+        unsigned tp = 0, wp = 0;
+        int ts = 0;
         for (int kb = it.z0;; kb += K::NU, tp ^= 1u) {
             // staging buffer of plane k: k & 1
             const unsigned se = (kb & 1) * Cfg::kStageBytes, sodd = Cfg::kStageBytes - se;
             if (!K::template planes<0>(wk, cx, br, ringA, ringB, maps, it, a, fc, se, sodd,
-                                       pu + (long long)(kb - it.z0) * cx.plane, kb, tp, rec))
+                                       pu + (long long)(kb - it.z0) * cx.plane, kb, tp, ts, wp,
+                                       rec))
                 break;
             K::rotate_queue(wk);
+            ts += K::NU;
+            if (ts >= NA) {
+                ts -= NA;
+                wp ^= 1u;
+            }
         }
     }
 
