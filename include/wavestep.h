@@ -281,8 +281,8 @@ int ws_forward(ws_t ws);
  * 4.1e-3; BF16 6.1e-3, 2.3e-2, 3.5e-2 (FP32 storage 5.3e-7 ... 1.9e-6): FP16
  * stays within 1e-2, BF16 only for about the first 100 steps (its 8-bit
  * significand's rounding errors add up like a random walk); at 1024^3 after
- * 100 steps FP16 7.6e-4, BF16 5.9e-3. Speed on the 1024^3 survey: 1.12x (FP16)
- * and 1.13x (BF16) of FP32 storage. This realizes the reduced-precision
+ * 100 steps FP16 7.6e-4, BF16 5.9e-3. Speed on the 1024^3 survey: 1.28x (FP16
+ * and BF16) of FP32 storage. This realizes the reduced-precision
  * storage that the paper contrasts with its FP32-only arithmetic (Section I). */
 int ws_set_storage(ws_t ws, int storage);
 
