@@ -181,25 +181,21 @@ struct Cfg16 {
         size_t(2) * kStageBytes + size_t(NA) * kSlotABytes + size_t(NB) * kSlotBBytes;
 };
 
-// 128-bit shared store.
-__device__ __forceinline__ void sts4(float *p, float4 v) {
-    asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(smem_addr(p)), "f"(v.x),
-                 "f"(v.y), "f"(v.z), "f"(v.w)
-                 : "memory");
-}
-
 struct Maps16 {
     CUtensorMap u, d, w;
 };
 
 // Shared-memory accesses at a 32-bit shared address plus a compile-time byte
-// offset from a per-thread base computed once per item (the sum is left to
+// offset (negative offsets wrap modulo 2^32, which is the same address) from
+// a per-thread base computed once per item (the sum is left to
 // the compiler: measured 1 % faster than the offset as an immediate in the
 // instruction text).
 template <int OFF>
 __device__ __forceinline__ uint2 lds2_at(unsigned a) {
     uint2 v;
-    asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "r"(a + OFF));
+    asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];"
+                 : "=r"(v.x), "=r"(v.y)
+                 : "r"(a + static_cast<unsigned>(OFF)));
     return v;
 }
 template <int OFF>
@@ -207,7 +203,7 @@ __device__ __forceinline__ float4 lds4_at(unsigned a) {
     float4 v;
     asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
                  : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-                 : "r"(a + OFF));
+                 : "r"(a + static_cast<unsigned>(OFF)));
     return v;
 }
 template <int OFF>
@@ -390,7 +386,11 @@ __device__ __forceinline__ void store16(uint16_t *p, const uint2 st) {
 
 // Planes per loop trip: 9 (the ring depth: every ring slot and queue index
 // is a compile-time constant) or 3 (a third of the code, with the queue
-// renamed by moves after each trip and the ring-A slots computed).
+// renamed by moves after each trip and the ring-A slots computed). 3 is the
+// default: the 9-plane loop body (~45 KB of code) does not stay in the
+// instruction caches, and warps waited 1.40 cycles per issued instruction
+// for instruction fetch against 0.25 with 3 planes (1024^3 FP16 441 -> 479
+// Gcell/s, for 24 more moves per plane).
 #ifndef WS16_TRIP
 #define WS16_TRIP 3
 #endif
@@ -642,8 +642,9 @@ struct Kern16 {
         wk.amax = Fmt::amax(Fmt::amax(wk.amax, su1.x), su1.y);
     }
 
-    // After a trip of 3 planes the queue holds planes k-1 .. k+7 in slots
-    // rotated by 3: rename them (the 9-plane trip needs no renaming).
+    // After a trip of 3 planes starting at plane kb the queue holds planes
+    // kb-1 .. kb+6 (the next trip's k-4 .. k+3) in slots rotated by 3:
+    // rename them (the 9-plane trip needs no renaming).
     static __device__ __forceinline__ void rotate_queue(Walk16 &wk) {
         if constexpr (NU % 9 != 0) {
             float4 t[9][2];
