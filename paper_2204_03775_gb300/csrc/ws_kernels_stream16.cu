@@ -141,9 +141,8 @@ struct Fp16Fmt {
 // y neighbours j-4..j-1 and j+2..j+5 serve both rows. Every thread computes:
 // there is no producer warp. Ring A (U of a plane with its halo) holds NA
 // planes, ring B (the D and W tiles of a plane) NB planes; a plane is
-// processed per loop step and NU = NA planes per loop trip, so every ring
-// slot and register-queue index is a compile-time constant (no queue
-// rotation, no slot arithmetic).
+// processed per loop step and NU planes per loop trip (see WS16_TRIP), so
+// the register-queue indices and ring-B slots are compile-time constants.
 template <int TX, int TY, int NA, int NB>
 struct Cfg16 {
     static constexpr int kCols = TX / 4;               // threads across a row
@@ -390,7 +389,8 @@ __device__ __forceinline__ void store16(uint16_t *p, const uint2 st) {
 // default: the 9-plane loop body (~45 KB of code) does not stay in the
 // instruction caches, and warps waited 1.40 cycles per issued instruction
 // for instruction fetch against 0.25 with 3 planes (1024^3 FP16 441 -> 479
-// Gcell/s, for 24 more moves per plane).
+// Gcell/s, for 24 more moves per plane; 6-plane trips, 12 moves per plane,
+// ran 471 against 497: fetch stalls again).
 #ifndef WS16_TRIP
 #define WS16_TRIP 3
 #endif
@@ -512,6 +512,7 @@ struct Kern16 {
         constexpr int SB = RQ % NB;
         // plane r fills ring-B slot SB for the (NU trip / 3 + RQ / 3)-th time
         constexpr unsigned PB = (RQ / NB) & 1u;
+        const unsigned pb = ((NU / NB) & 1 ? tp : 0u) ^ PB;
         constexpr int OB = SB * Cfg::kSlotBBytes;
         constexpr int RA = Cfg::kRowW * 2, RB = TX * 2, WB = Cfg::kTile * 2, RS = Cfg::kSW * 4;
         const int r = k - cx.z0;
@@ -525,7 +526,7 @@ struct Kern16 {
             sa_own = (RQ + 8) % NA;
             sa_halo = (RQ + 4) % NA;
             pa = wp ^ (((RQ + 8) / NA) & 1u);
-        } else {
+        } else {   // ts in {0, 3, 6}: ts + RQ + 8 < 18
             const bool wrap = ts + RQ + 8 >= NA;
             sa_own = wrap ? ts + RQ + 8 - NA : ts + RQ + 8;
             sa_halo = ts + RQ + 4 >= NA ? ts + RQ + 4 - NA : ts + RQ + 4;
@@ -535,9 +536,9 @@ struct Kern16 {
 
         // U of plane k + 4 (ring A) and D, W of plane k (ring B): one test of
         // both barriers, the bounded waits only when either is not complete
-        if (!(mbar_try_wait(&br.fullA[sa_own], pa) & mbar_try_wait(&br.fullB[SB], tp ^ PB)))
+        if (!(mbar_try_wait(&br.fullA[sa_own], pa) & mbar_try_wait(&br.fullB[SB], pb)))
             wk.ok = wait_phase(&br.fullA[sa_own], pa, &br.abort, a.status) &&
-                    wait_phase(&br.fullB[SB], tp ^ PB, &br.abort, a.status) && wk.ok;
+                    wait_phase(&br.fullB[SB], pb, &br.abort, a.status) && wk.ok;
         // this thread's two rows of plane k + 4 -> the queue (decoded once)
         wk.q[Q8][0] = Fmt::decode(lds2_at<0>(cx.aOwn + oa_own));
         wk.q[Q8][1] = Fmt::decode(lds2_at<RA>(cx.aOwn + oa_own));
@@ -642,9 +643,9 @@ struct Kern16 {
         wk.amax = Fmt::amax(Fmt::amax(wk.amax, su1.x), su1.y);
     }
 
-    // After a trip of 3 planes starting at plane kb the queue holds planes
-    // kb-1 .. kb+6 (the next trip's k-4 .. k+3) in slots rotated by 3:
-    // rename them (the 9-plane trip needs no renaming).
+    // After a trip of NU planes starting at plane kb the queue holds planes
+    // kb+NU-4 .. kb+NU+3 (the next trip's k-4 .. k+3) in slots rotated by
+    // NU: rename them (the 9-plane trip needs no renaming).
     static __device__ __forceinline__ void rotate_queue(Walk16 &wk) {
         if constexpr (NU % 9 != 0) {
             float4 t[9][2];
