@@ -100,6 +100,22 @@ def test_ragged_layered_with_sponge(kernel, tile, zb):
     assert_parity(tr, ref["traces"])
 
 
+@pytest.mark.parametrize("tile", [(64, 8), (32, 16), (32, 8)])
+def test_stream_z_blocks_of_every_length_agree_bitwise(tile):
+    """The streaming kernel walks an item's planes three at a time through
+    rings of 8 (ring A) and 4 (ring B) slots: items of 1 to 13 planes end a
+    trip early at every phase and wrap the rings a different number of times.
+    Every z block gives the same bits as the direct kernel."""
+    w = _ragged_workload(nt=40)
+    _, u1, p1, t1 = run_gpu(w, kernel=wsb.WS_KERNEL_DIRECT)
+    for zb in (1, 2, 3, 4, 5, 6, 7, 8, 9, 11, 13):
+        h, u2, p2, t2 = run_gpu(w, kernel=wsb.WS_KERNEL_STREAM, tile=tile, zblock=zb)
+        wsb.ws_destroy(h)
+        np.testing.assert_array_equal(u1, u2, err_msg=f"zblock {zb}")
+        np.testing.assert_array_equal(p1, p2, err_msg=f"zblock {zb}")
+        np.testing.assert_array_equal(t1, t2, err_msg=f"zblock {zb}")
+
+
 def test_direct_and_stream_agree_bitwise():
     w = _ragged_workload(nt=60)
     _, u1, p1, t1 = run_gpu(w, kernel=wsb.WS_KERNEL_DIRECT)
