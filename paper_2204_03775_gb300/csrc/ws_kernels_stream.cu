@@ -155,7 +155,6 @@ struct BatchView {
     Geom g;
     const float *gx, *gy, *gz;
     float *out;
-    static constexpr long long lap_delta = 0;
     const int *rec_ptr;
     const BatchShot *shot;
     int t;
